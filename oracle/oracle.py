@@ -1,0 +1,188 @@
+"""Python face of the CPU oracle (``sc_oracle.c``) and of the brute-force
+second-quantized Hamiltonian (``fci_brute.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and
+the benchmark's CPU-baseline leg.  The library never imports it.  The C sources
+are compiled with gcc on first use into ``oracle/_build/``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = None
+_LOCK = threading.Lock()
+
+_SOURCES = ("sc_oracle.c", "fci_brute.c")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library; returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, "liboracle.so")
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if not force and os.path.exists(out) and all(
+            os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            I = ctypes.c_int
+            D = ctypes.c_double
+            lib.orc_count.restype = I64
+            lib.orc_count.argtypes = [I, I, I, P, P, D, P, I64, D, P]
+            lib.orc_gen.restype = None
+            lib.orc_gen.argtypes = [I, I, I, P, P, D, P, I64, D, P, P, P]
+            lib.orc_dedup.restype = I64
+            lib.orc_dedup.argtypes = [P, I64, I, P, P]
+            lib.orc_hpsi.restype = None
+            lib.orc_hpsi.argtypes = [I, I, I, P, P, D, P, I64, P, D, P]
+            lib.orc_energy_reduce.restype = None
+            lib.orc_energy_reduce.argtypes = [P, P, I64, P, P]
+            lib.orc_energy_grad.restype = None
+            lib.orc_energy_grad.argtypes = [P, P, I64, D, D, D, P]
+            lib.orc_apply_op.restype = I
+            lib.orc_apply_op.argtypes = [P, I, I]
+            lib.orc_threads.restype = I
+            lib.fci_brute_H.restype = I64
+            lib.fci_brute_H.argtypes = [I, P, P, D, P, I64, I, P]
+            lib.fci_brute_column.restype = I64
+            lib.fci_brute_column.argtypes = [I, P, P, D, P, I64, I, P, P]
+            _LIB = lib
+    return _LIB
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class OracleSystem:
+    """Integrals plus electron counts, held as contiguous FP64 arrays."""
+
+    def __init__(self, norb, n_alpha, n_beta, h1, h2, ecore=0.0):
+        self.norb, self.n_alpha, self.n_beta = int(norb), int(n_alpha), int(n_beta)
+        self.h1 = _c(h1, np.float64).reshape(norb, norb)
+        self.h2 = _c(h2, np.float64).reshape((norb,) * 4)
+        self.ecore = float(ecore)
+        self.W = (2 * norb + 63) // 64
+
+    @classmethod
+    def of(cls, system):
+        return cls(system.norb, system.n_alpha, system.n_beta, system.h1, system.h2,
+                   getattr(system, "ecore", 0.0))
+
+    def _head(self):
+        return (self.norb, self.n_alpha, self.n_beta, _p(self.h1), _p(self.h2), self.ecore)
+
+    def count(self, dets, eps):
+        dets = _c(dets, np.uint64).reshape(-1, self.W)
+        counts = np.zeros(dets.shape[0], dtype=np.int64)
+        _lib().orc_count(*self._head(), _p(dets), dets.shape[0], float(eps), _p(counts))
+        return counts
+
+    def gen(self, dets, eps, counts=None):
+        """Coupled lists in CSR form: (offsets[n+1], target dets[total, W], H[total])."""
+        dets = _c(dets, np.uint64).reshape(-1, self.W)
+        if counts is None:
+            counts = self.count(dets, eps)
+        offsets = np.zeros(dets.shape[0] + 1, dtype=np.int64)
+        np.cumsum(counts, out=offsets[1:])
+        total = int(offsets[-1])
+        out_d = np.zeros((total, self.W), dtype=np.uint64)
+        out_h = np.zeros(total, dtype=np.float64)
+        _lib().orc_gen(*self._head(), _p(dets), dets.shape[0], float(eps), _p(offsets),
+                       _p(out_d), _p(out_h))
+        return offsets, out_d, out_h
+
+    def hpsi(self, S, psi, eps):
+        S = _c(S, np.uint64).reshape(-1, self.W)
+        psi = _c(psi, np.float64)
+        out = np.zeros(S.shape[0], dtype=np.float64)
+        _lib().orc_hpsi(*self._head(), _p(S), S.shape[0], _p(psi), float(eps), _p(out))
+        return out
+
+    def energy(self, S, psi, eps, g=1.0):
+        """(E, norm2, Hpsi, grad) of E = psi.H psi / psi.psi over the set S."""
+        psi = _c(psi, np.float64)
+        hp = self.hpsi(S, psi, eps)
+        E = np.zeros(1)
+        n2 = np.zeros(1)
+        _lib().orc_energy_reduce(_p(psi), _p(hp), psi.size, _p(E), _p(n2))
+        grad = np.zeros_like(psi)
+        _lib().orc_energy_grad(_p(psi), _p(hp), psi.size, float(E[0]), float(n2[0]), float(g),
+                               _p(grad))
+        return float(E[0]), float(n2[0]), hp, grad
+
+
+def dedup(keys, W=None):
+    """(unique[n_unique, W], inverse[total]) of W-word keys."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    if keys.ndim == 1:
+        keys = keys.reshape(-1, 1 if W is None else W)
+    keys = np.ascontiguousarray(keys)
+    total, W = keys.shape
+    uniq = np.zeros((total, W), dtype=np.uint64)
+    inv = np.zeros(total, dtype=np.int64)
+    nu = _lib().orc_dedup(_p(keys), total, W, _p(uniq), _p(inv))
+    if nu < 0:
+        raise MemoryError("oracle dedup: allocation failed")
+    return uniq[:nu].copy(), inv
+
+
+def apply_op(det, s, create):
+    """(phase, new det) of a+_s (create) or a_s on one determinant."""
+    d = _c(det, np.uint64).copy()
+    ph = _lib().orc_apply_op(_p(d), int(s), int(bool(create)))
+    return ph, d
+
+
+def brute_hamiltonian(norb, h1, h2, basis, ecore=0.0):
+    """Dense H over a sorted basis by term-by-term second quantization."""
+    basis = _c(basis, np.uint64)
+    if basis.ndim == 1:
+        basis = basis.reshape(-1, 1)
+    n, W = basis.shape
+    H = np.zeros((n, n), dtype=np.float64)
+    outside = _lib().fci_brute_H(int(norb), _p(_c(h1, np.float64)), _p(_c(h2, np.float64)),
+                                 float(ecore), _p(basis), n, W, _p(H))
+    return H, int(outside)
+
+
+def brute_column(norb, h1, h2, basis, det, ecore=0.0):
+    """Column <basis_r|H|det> over a sorted basis by second quantization; returns
+    (column, number of operator strings that left the basis)."""
+    basis = _c(basis, np.uint64)
+    if basis.ndim == 1:
+        basis = basis.reshape(-1, 1)
+    n, W = basis.shape
+    det = _c(det, np.uint64).reshape(W)
+    col = np.zeros(n, dtype=np.float64)
+    outside = _lib().fci_brute_column(int(norb), _p(_c(h1, np.float64)), _p(_c(h2, np.float64)),
+                                      float(ecore), _p(basis), n, W, _p(det), _p(col))
+    return col, int(outside)
+
+
+def threads() -> int:
+    return int(_lib().orc_threads())
