@@ -1,0 +1,172 @@
+/*
+ * cusci.h -- C ABI of libcusci: coupled-configuration generation with
+ * Slater-Condon matrix elements, |H_ij| screening, in-batch de-duplication and
+ * the variational energy with its adjoint, for selected configuration
+ * interaction driven by neural-network quantum states (NNQS-SCI, Stage 1 and
+ * Stage 3 of the paper's pipeline, Sec. 3; kernels of Sec. 4.1-4.2).
+ *
+ * Data model (Sec. 2.1; the paper fixes no spin-orbital order, this library
+ * takes the interleaved one):
+ *   - norb spatial orbitals, M = 2*norb spin orbitals, spin orbital
+ *     s = 2*p + sigma with sigma = 0 for alpha, 1 for beta.
+ *   - A determinant is W = ceil(M/64) little-endian uint64 words; spin orbital
+ *     s is bit (s & 63) of word (s >> 6).  W is 1 or 2 (norb <= 64).
+ *   - Arrays of determinants are row-major [n][W].  "Sorted" means ascending as
+ *     W-word unsigned integers, word W-1 most significant.
+ *   - Integrals are real: h1[p*norb+q] symmetric, h2 in chemists' notation,
+ *     h2[((p*norb+q)*norb+r)*norb+s] = (pq|rs) with the 8-fold symmetry.
+ *   - H = Ecore + sum h_pq a+_{p s} a_{q s}
+ *           + 1/2 sum (pq|rs) a+_{p s} a+_{r t} a_{s t} a_{q s};
+ *     a_s and a+_s carry the phase (-1)^(occupied spin orbitals below s).
+ *
+ * Coupled set C_i of a source determinant (Sec. 2.1: every j with H_ij != 0,
+ * reached by moving one or two electrons, j = i included), in canonical order:
+ * the diagonal first (always kept); then singles i->a with occupied i
+ * ascending and same-spin virtual a ascending; then doubles with occupied pairs
+ * i<j lexicographic and (a,b) lexicographic (a<b when i and j share a spin, a of
+ * i's spin and b of j's spin otherwise).  Off-diagonal entries are kept iff
+ * |H_ij| > eps (the screening test of Algorithm 1; eps < 0 keeps all).
+ * Matrix elements are FP64 and bit-identical to the Slater-Condon closed forms
+ * summed in the order: diagonal (Ecore + sum_i h_ii) + sum_{i<j}[(ii|jj) -
+ * same-spin (ij|ji)]; single h_ai then, for k in O ascending (k != i), +(ai|kk)
+ * and, for k of a's spin, -(ak|ki); double (ai|bj) - (aj|bi) for a same-spin
+ * pair, (ai|bj) otherwise.
+ *
+ * Conventions of every call:
+ *   - The caller owns every buffer it passes (device pointers are prefixed d_,
+ *     host pointers h_); the library owns only cusci_system objects and what
+ *     they hold.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated.
+ *   - Nothing aborts or traps.  Every call returns a status; the message of the
+ *     last failure on the calling thread is cusci_last_error().
+ *   - A cusci_system may be used from several streams only if the calls are
+ *     ordered between them by the caller (its screening-mask cache is shared).
+ *   - Requires a GPU of compute capability 10.3 (the library is built for
+ *     sm_103a only).
+ */
+#ifndef CUSCI_H
+#define CUSCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CUSCI_OK = 0,
+    CUSCI_ERR_INVALID = 1,     /* bad argument or precondition violated          */
+    CUSCI_ERR_OOM = 2,         /* device / host allocation or workspace too small */
+    CUSCI_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
+    CUSCI_ERR_OVERFLOW = 4,    /* output capacity / offsets inconsistent          */
+    CUSCI_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
+    CUSCI_ERR_UNSUPPORTED = 6  /* size outside what this build handles            */
+} cusci_status;
+
+typedef struct cusci_system cusci_system; /* opaque, library-owned */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *cusci_last_error(void);
+/* Library version string. */
+const char *cusci_version(void);
+
+/* ------------------------------------------------------------------ system
+ * Builds the device-side integral tables of one molecular system (the
+ * excitation tables T_single / T_double of Sec. 4.2.1, held here as permuted
+ * FP64 slabs plus per-eps screening bitmasks).  h1: host, norb*norb doubles.
+ * h2: host, norb^4 doubles.  Both are copied; the caller may free them on
+ * return.  1 <= norb <= 64, 0 <= n_alpha, n_beta <= norb.  Synchronous.
+ * Errors: CUSCI_ERR_INVALID (sizes), CUSCI_ERR_OOM, CUSCI_ERR_CUDA. */
+cusci_status cusci_system_create(int norb, int n_alpha, int n_beta, const double *h1,
+                                 const double *h2, double ecore, cusci_system **out);
+void cusci_system_destroy(cusci_system *sys);
+/* W of the system's determinants (1 or 2); 0 for NULL. */
+int cusci_system_words(const cusci_system *sys);
+
+/* ------------------------------------------------------------------ generation
+ * Count pass (the "count" half of count-then-fill, Sec. 4.2.2; it replaces the
+ * g_counter slab reservation of Algorithm 1).
+ * d_dets: device [n][W] sources.  Bits at or above M are ignored; the coupled
+ * set is that of the occupation the bits describe (use cusci_check_dets to
+ * enforce the system's electron counts).  d_counts: device int64[n], receives
+ * |C_i| after screening, diagonal included.  n == 0 is a no-op. */
+cusci_status cusci_count_coupled(const cusci_system *sys, const uint64_t *d_dets, int64_t n,
+                                 double eps, int64_t *d_counts, void *stream);
+
+/* Exclusive prefix sum: d_offsets[0] = 0, d_offsets[k+1] = d_offsets[k] +
+ * d_counts[k] (device int64, n+1 entries).  d_total (device, nullable) receives
+ * d_offsets[n].  Workspace: cusci_scan_workspace bytes of device memory. */
+cusci_status cusci_scan_workspace(int64_t n, size_t *bytes);
+cusci_status cusci_exclusive_scan(const int64_t *d_counts, int64_t n, int64_t *d_offsets,
+                                  void *d_ws, size_t ws_bytes, void *stream);
+
+/* Fill pass (Algorithm 1 and Sec. 4.2.2): writes C_i to rows
+ * [d_offsets[i], d_offsets[i+1]) of d_out_dets (device [total][W]) and d_out_h
+ * (device double[total]) in canonical order.  d_offsets must be the exclusive
+ * scan of the counts of the same sources at the same eps; a row range that
+ * does not match the regenerated count is reported through d_status.
+ * d_status: device int32 (nullable); set to CUSCI_ERR_OVERFLOW if any source's
+ * range disagrees (the rows of such a source are then left partly unwritten),
+ * untouched otherwise. */
+cusci_status cusci_gen_coupled(const cusci_system *sys, const uint64_t *d_dets, int64_t n,
+                               double eps, const int64_t *d_offsets, uint64_t *d_out_dets,
+                               double *d_out_h, int32_t *d_status, void *stream);
+
+/* Validates sources: d_status (device int32) is set to CUSCI_ERR_INVALID if any
+ * row has the wrong alpha/beta electron counts or a bit at or above M,
+ * untouched otherwise. */
+cusci_status cusci_check_dets(const cusci_system *sys, const uint64_t *d_dets, int64_t n,
+                              int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------ de-duplication
+ * In-batch de-duplication (Sec. 4.1 local sort + unique; Sec. 3 reverse index):
+ * d_unique receives the sorted distinct keys (capacity total*W words),
+ * d_inverse[k] the position of key k in d_unique (int32 if index_bytes == 4,
+ * int64 if 8; int32 requires total < 2^31).  n_ones >= 0 declares that every
+ * key has exactly n_ones set bits among its low n_bits bits, which lets the
+ * sort run on the keys' combinatorial rank (fewer radix passes); n_ones < 0
+ * sorts the raw low n_bits bits.  1 <= n_bits <= 64*W, W in {1,2}.
+ * d_n_unique: device int64 receiving the distinct count.  h_n_unique: host,
+ * nullable; if given, the call synchronizes the stream and writes it there.
+ * d_status: device int32, nullable: CUSCI_ERR_INVALID if a key breaks the
+ * n_ones declaration (outputs then undefined).
+ * Workspace: cusci_dedup_workspace bytes of device memory, 256-byte aligned. */
+cusci_status cusci_dedup_workspace(int64_t total, int W, int n_bits, int n_ones, size_t *bytes);
+cusci_status cusci_dedup(const uint64_t *d_keys, int64_t total, int W, int n_bits, int n_ones,
+                         void *d_ws, size_t ws_bytes, uint64_t *d_unique, void *d_inverse,
+                         int index_bytes, int64_t *d_n_unique, int64_t *h_n_unique,
+                         int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------ energy
+ * Variational energy over a selected set S (Eq. 1 restricted to S, Sec. 2.1;
+ * Stage 3 of Sec. 3): (H psi)_i = sum over j in C_i(eps) with j in S of
+ * H_ij psi_j, E = psi.(H psi) / psi.psi.  The coupled lists are regenerated,
+ * never stored (the just-in-time reverse index of Sec. 4.3).
+ * d_S: device [nS][W], strictly ascending, nS >= 1.  d_psi: device double[nS].
+ * d_E, d_norm2: device double[1].  d_Hpsi: device double[nS], nullable (H psi
+ * is then kept only in the workspace).  d_status (device int32, nullable): set
+ * to CUSCI_ERR_INVALID if S is not strictly ascending (results then undefined).
+ * Workspace: cusci_energy_workspace bytes of device memory, 256-byte aligned;
+ * it holds a hash table of S and is overwritten by every call.
+ * The reductions are deterministic (fixed order, no atomics). */
+cusci_status cusci_energy_workspace(const cusci_system *sys, int64_t nS, size_t *bytes);
+cusci_status cusci_energy_fwd(const cusci_system *sys, const uint64_t *d_S, int64_t nS,
+                              const double *d_psi, double eps, double *d_E, double *d_norm2,
+                              double *d_Hpsi, void *d_ws, size_t ws_bytes, int32_t *d_status,
+                              void *stream);
+/* Adjoint (Sec. 3 Stage 3, backpropagation of the energy):
+ * d_grad[i] = g * 2 ((H psi)_i - E psi_i) / norm2, with E and norm2 from the
+ * forward call and g = *d_grad_out (device double; NULL means 1).  d_Hpsi may
+ * be NULL, in which case H psi is recomputed from the coupled lists. */
+cusci_status cusci_energy_bwd(const cusci_system *sys, const uint64_t *d_S, int64_t nS,
+                              const double *d_psi, double eps, const double *d_E,
+                              const double *d_norm2, const double *d_Hpsi,
+                              const double *d_grad_out, double *d_grad, void *d_ws,
+                              size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUSCI_H */

@@ -1,0 +1,29 @@
+// Error reporting and version of the C ABI.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "cusci_internal.cuh"
+
+namespace {
+thread_local char g_last_error[512] = "";
+}
+
+namespace cusci {
+
+cusci_status fail(cusci_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+cusci_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? CUSCI_ERR_OOM : CUSCI_ERR_CUDA, "%s: %s (%s)",
+                what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+}  // namespace cusci
+
+extern "C" const char *cusci_last_error(void) { return g_last_error; }
+extern "C" const char *cusci_version(void) { return "cusci 0.1 (sm_103a)"; }

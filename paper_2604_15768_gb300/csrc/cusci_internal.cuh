@@ -1,0 +1,91 @@
+// Internal declarations shared by the libcusci translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cusci.h"
+
+#define CUSCI_MAX_NORB 64
+#define CUSCI_MASK_SLOTS 4
+
+namespace cusci {
+
+// One cached set of screening bitmasks for a given eps.
+// bits[((kind*norb + pi)*norb + pj)*norb + pa] has bit pb set iff the double
+// excitation with spatial occupied (pi, pj) and virtual (pa, pb) survives
+// |H| > eps; kind 0 = both electrons of one spin (only pi < pj, pa < pb are
+// set), kind 1 = opposite spins.
+struct MaskSlot {
+    double eps;
+    uint64_t *bits;
+    uint64_t stamp;
+    bool valid;
+};
+
+}  // namespace cusci
+
+struct cusci_system {
+    int norb, n_alpha, n_beta, W, M;
+    double ecore;
+    int device;
+    // device tables, all FP64, spatial indices
+    double *h1;   // [p][q]
+    double *J;    // [p][q] = (pp|qq)
+    double *K;    // [p][q] = (pq|qp)
+    double *S1;   // [pa][pi][pk] = (pa pi|pk pk)
+    double *S2;   // [pa][pi][pk] = (pa pk|pk pi)
+    double *T;    // [kind][pi][pj][pa][pb]: kind 0 (ai|bj)-(aj|bi), kind 1 (ai|bj)
+    cusci::MaskSlot masks[CUSCI_MASK_SLOTS];
+    uint64_t clock;
+};
+
+namespace cusci {
+
+// thread-local error message plumbing (capi.cu)
+cusci_status fail(cusci_status st, const char *fmt, ...);
+cusci_status cuda_fail(cudaError_t e, const char *what);
+
+// returns the screening masks for eps, building them on `stream` if needed
+cusci_status masks_for(cusci_system *sys, double eps, cudaStream_t stream,
+                       const uint64_t **out);
+
+// device view of a system for kernels
+struct SysView {
+    int norb, M, W;
+    double ecore;
+    const double *__restrict__ h1;
+    const double *__restrict__ J;
+    const double *__restrict__ K;
+    const double *__restrict__ S1;
+    const double *__restrict__ S2;
+    const double *__restrict__ T;
+    const uint64_t *__restrict__ mask;
+};
+
+inline SysView view_of(const cusci_system *s, const uint64_t *mask) {
+    SysView v;
+    v.norb = s->norb; v.M = s->M; v.W = s->W; v.ecore = s->ecore;
+    v.h1 = s->h1; v.J = s->J; v.K = s->K; v.S1 = s->S1; v.S2 = s->S2; v.T = s->T;
+    v.mask = mask;
+    return v;
+}
+
+inline int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace cusci
+
+#define CUSCI_CHECK_LAUNCH(what)                                   \
+    do {                                                          \
+        cudaError_t _e = cudaGetLastError();                      \
+        if (_e != cudaSuccess) return cusci::cuda_fail(_e, what); \
+    } while (0)

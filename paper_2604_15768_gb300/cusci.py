@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libcusci (the C ABI in ``include/cusci.h``).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  Determinants travel as
+``torch.int64`` tensors of shape (n, W) holding the uint64 bit patterns.
+
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+__all__ = ["CusciError", "load", "System", "count_coupled", "exclusive_scan", "gen_coupled",
+           "check_dets", "dedup", "coupled", "energy_fwd", "energy_bwd", "Energy"]
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+
+_LIB = None
+_LOCK = threading.Lock()
+
+STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "OVERFLOW", 5: "TIMEOUT",
+          6: "UNSUPPORTED"}
+
+
+class CusciError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: CUSCI_ERR_{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_PROTOS = {
+    "cusci_last_error": (ctypes.c_char_p, []),
+    "cusci_version": (ctypes.c_char_p, []),
+    "cusci_system_create": (_I, [_I, _I, _I, _P, _P, _D, ctypes.POINTER(_P)]),
+    "cusci_system_destroy": (None, [_P]),
+    "cusci_system_words": (_I, [_P]),
+    "cusci_count_coupled": (_I, [_P, _P, _I64, _D, _P, _P]),
+    "cusci_scan_workspace": (_I, [_I64, ctypes.POINTER(_SZ)]),
+    "cusci_exclusive_scan": (_I, [_P, _I64, _P, _P, _SZ, _P]),
+    "cusci_gen_coupled": (_I, [_P, _P, _I64, _D, _P, _P, _P, _P, _P]),
+    "cusci_check_dets": (_I, [_P, _P, _I64, _P, _P]),
+    "cusci_dedup_workspace": (_I, [_I64, _I, _I, _I, ctypes.POINTER(_SZ)]),
+    "cusci_dedup": (_I, [_P, _I64, _I, _I, _I, _P, _SZ, _P, _P, _I, _P, _P, _P, _P]),
+    "cusci_energy_workspace": (_I, [_P, _I64, ctypes.POINTER(_SZ)]),
+    "cusci_energy_fwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _SZ, _P, _P]),
+    "cusci_energy_bwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+}
+
+
+def exported_names() -> list[str]:
+    return sorted(_PROTOS)
+
+
+def load(path: str | None = None):
+    """Load (building first if needed) libcusci.so and declare its prototypes."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = path or _build.LIB
+            if not os.path.exists(path):
+                path = _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _PROTOS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = lib
+    return _LIB
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise CusciError(rc, where, load().cusci_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+def dets_to_device(dets: np.ndarray, device="cuda") -> torch.Tensor:
+    """(n, W) uint64 numpy array -> int64 CUDA tensor with the same bits."""
+    a = np.ascontiguousarray(dets, dtype=np.uint64)
+    return torch.from_numpy(a.view(np.int64)).to(device)
+
+
+def dets_to_numpy(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+class System:
+    """A molecular system resident on the current CUDA device (library-owned)."""
+
+    def __init__(self, norb, n_alpha, n_beta, h1, h2, ecore=0.0):
+        lib = load()
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        h2 = np.ascontiguousarray(h2, dtype=np.float64)
+        if h1.size != norb * norb or h2.size != norb ** 4:
+            raise ValueError("integral sizes do not match norb")
+        handle = ctypes.c_void_p()
+        _check(lib.cusci_system_create(int(norb), int(n_alpha), int(n_beta),
+                                       h1.ctypes.data_as(_P), h2.ctypes.data_as(_P),
+                                       float(ecore), ctypes.byref(handle)),
+               "cusci_system_create")
+        self._h = handle
+        self.norb, self.n_alpha, self.n_beta = int(norb), int(n_alpha), int(n_beta)
+        self.W = lib.cusci_system_words(handle)
+        self.M = 2 * self.norb
+
+    @classmethod
+    def of(cls, s):
+        return cls(s.norb, s.n_alpha, s.n_beta, s.h1, s.h2, getattr(s, "ecore", 0.0))
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("system destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _LIB is not None:
+            _LIB.cusci_system_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def count_coupled(sys: System, dets: torch.Tensor, eps: float, out=None, stream=None):
+    dets = _dev(dets, torch.int64, "dets")
+    n = dets.shape[0]
+    out = out if out is not None else torch.empty(n, dtype=torch.int64, device=dets.device)
+    _check(load().cusci_count_coupled(sys.handle, _ptr(dets), n, float(eps), _ptr(out),
+                                      _stream(stream)), "cusci_count_coupled")
+    return out
+
+
+def exclusive_scan(counts: torch.Tensor, out=None, stream=None):
+    counts = _dev(counts, torch.int64, "counts")
+    n = counts.shape[0]
+    lib = load()
+    ws = ctypes.c_size_t()
+    _check(lib.cusci_scan_workspace(n, ctypes.byref(ws)), "cusci_scan_workspace")
+    wbuf = torch.empty(max(1, ws.value), dtype=torch.uint8, device=counts.device)
+    out = out if out is not None else torch.empty(n + 1, dtype=torch.int64, device=counts.device)
+    _check(lib.cusci_exclusive_scan(_ptr(counts), n, _ptr(out), _ptr(wbuf), ws.value,
+                                    _stream(stream)), "cusci_exclusive_scan")
+    return out
+
+
+def gen_coupled(sys: System, dets: torch.Tensor, eps: float, offsets: torch.Tensor, total: int,
+                out_dets=None, out_h=None, status=None, stream=None):
+    dets = _dev(dets, torch.int64, "dets")
+    offsets = _dev(offsets, torch.int64, "offsets")
+    dev = dets.device
+    if out_dets is None:
+        out_dets = torch.empty((total, sys.W), dtype=torch.int64, device=dev)
+    if out_h is None:
+        out_h = torch.empty(total, dtype=torch.float64, device=dev)
+    _check(load().cusci_gen_coupled(sys.handle, _ptr(dets), dets.shape[0], float(eps),
+                                    _ptr(offsets), _ptr(out_dets), _ptr(out_h), _ptr(status),
+                                    _stream(stream)), "cusci_gen_coupled")
+    return out_dets, out_h
+
+
+def check_dets(sys: System, dets: torch.Tensor, status: torch.Tensor, stream=None):
+    dets = _dev(dets, torch.int64, "dets")
+    _check(load().cusci_check_dets(sys.handle, _ptr(dets), dets.shape[0], _ptr(status),
+                                   _stream(stream)), "cusci_check_dets")
+    return status
+
+
+def dedup_workspace(total: int, W: int, n_bits: int, n_ones: int) -> int:
+    ws = ctypes.c_size_t()
+    _check(load().cusci_dedup_workspace(int(total), int(W), int(n_bits), int(n_ones),
+                                        ctypes.byref(ws)), "cusci_dedup_workspace")
+    return ws.value
+
+
+def dedup(keys: torch.Tensor, n_bits: int, n_ones: int = -1, index_bytes: int = 4,
+          workspace=None, status=None, stream=None, sync=True):
+    """Sorted distinct keys and the inverse index.  Returns (unique, inverse, n_unique);
+    with ``sync=False`` n_unique is a device tensor and ``unique`` is full capacity."""
+    keys = _dev(keys, torch.int64, "keys")
+    total, W = keys.shape
+    dev = keys.device
+    need = dedup_workspace(total, W, n_bits, n_ones)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    unique = torch.empty((max(total, 1), W), dtype=torch.int64, device=dev)
+    inverse = torch.empty(max(total, 1), dtype=torch.int32 if index_bytes == 4 else torch.int64,
+                          device=dev)
+    d_nu = torch.zeros(1, dtype=torch.int64, device=dev)
+    h_nu = ctypes.c_int64(-1)
+    _check(load().cusci_dedup(_ptr(keys), total, W, int(n_bits), int(n_ones), _ptr(workspace),
+                              workspace.numel(), _ptr(unique), _ptr(inverse), int(index_bytes),
+                              _ptr(d_nu), ctypes.byref(h_nu) if sync else None, _ptr(status),
+                              _stream(stream)), "cusci_dedup")
+    if sync:
+        return unique[:h_nu.value], inverse[:total], h_nu.value
+    return unique, inverse[:total], d_nu
+
+
+def coupled(sys: System, dets: torch.Tensor, eps: float, stream=None):
+    """count -> scan -> fill.  Returns (offsets, out_dets, out_h, status)."""
+    counts = count_coupled(sys, dets, eps, stream=stream)
+    offsets = exclusive_scan(counts, stream=stream)
+    total = int(offsets[-1].item())
+    status = torch.zeros(1, dtype=torch.int32, device=dets.device)
+    out_d, out_h = gen_coupled(sys, dets, eps, offsets, total, status=status, stream=stream)
+    return offsets, out_d, out_h, status
+
+
+def energy_workspace(sys: System, nS: int) -> int:
+    ws = ctypes.c_size_t()
+    _check(load().cusci_energy_workspace(sys.handle, int(nS), ctypes.byref(ws)),
+           "cusci_energy_workspace")
+    return ws.value
+
+
+def energy_fwd(sys: System, S: torch.Tensor, psi: torch.Tensor, eps: float, save_hpsi=True,
+               workspace=None, status=None, stream=None):
+    """Returns (E, norm2, Hpsi or None) as device tensors."""
+    S = _dev(S, torch.int64, "S")
+    psi = _dev(psi, torch.float64, "psi")
+    nS = S.shape[0]
+    dev = S.device
+    need = energy_workspace(sys, nS)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    n2 = torch.empty(1, dtype=torch.float64, device=dev)
+    hp = torch.empty(nS, dtype=torch.float64, device=dev) if save_hpsi else None
+    _check(load().cusci_energy_fwd(sys.handle, _ptr(S), nS, _ptr(psi), float(eps), _ptr(E),
+                                   _ptr(n2), _ptr(hp), _ptr(workspace), workspace.numel(),
+                                   _ptr(status), _stream(stream)), "cusci_energy_fwd")
+    return E, n2, hp
+
+
+def energy_bwd(sys: System, S, psi, eps, E, norm2, hpsi=None, grad_out=None, workspace=None,
+               stream=None):
+    S = _dev(S, torch.int64, "S")
+    psi = _dev(psi, torch.float64, "psi")
+    nS = S.shape[0]
+    dev = S.device
+    if hpsi is None and (workspace is None or workspace.numel() < energy_workspace(sys, nS)):
+        workspace = torch.empty(energy_workspace(sys, nS), dtype=torch.uint8, device=dev)
+    grad = torch.empty(nS, dtype=torch.float64, device=dev)
+    g = None
+    if grad_out is not None:
+        g = grad_out.reshape(1).to(dtype=torch.float64).contiguous()
+    _check(load().cusci_energy_bwd(sys.handle, _ptr(S), nS, _ptr(psi), float(eps), _ptr(E),
+                                   _ptr(norm2), _ptr(hpsi), _ptr(g), _ptr(grad),
+                                   _ptr(workspace), 0 if workspace is None else workspace.numel(),
+                                   _stream(stream)), "cusci_energy_bwd")
+    return grad
+
+
+class Energy(torch.autograd.Function):
+    """E(psi) = psi.H psi / psi.psi over the sorted set S, with the hand-written
+    adjoint dE/dpsi = 2 (H psi - E psi) / psi.psi.  ``recompute=True`` keeps no
+    H psi between forward and backward (the coupled lists are regenerated)."""
+
+    @staticmethod
+    def forward(ctx, psi, system, S, eps, recompute=False):
+        E, n2, hp = energy_fwd(system, S, psi, eps, save_hpsi=not recompute)
+        ctx.system, ctx.eps, ctx.recompute = system, eps, recompute
+        if recompute:
+            ctx.save_for_backward(psi, S, E, n2)
+        else:
+            ctx.save_for_backward(psi, S, E, n2, hp)
+        return E.reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        if ctx.recompute:
+            psi, S, E, n2 = ctx.saved_tensors
+            hp = None
+        else:
+            psi, S, E, n2, hp = ctx.saved_tensors
+        grad = energy_bwd(ctx.system, S, psi, ctx.eps, E, n2, hpsi=hp, grad_out=g)
+        return grad, None, None, None, None

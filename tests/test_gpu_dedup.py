@@ -1,0 +1,96 @@
+"""GPU parity of the de-duplication (sorted distinct keys + inverse index) with
+the CPU oracle, bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2604_15768_gb300 import cusci, synth
+from tests.gpu_util import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_dedup(keys, n_bits, n_ones, index_bytes=4):
+    u, inv, nu = cusci.dedup(to_dev(keys), n_bits, n_ones, index_bytes=index_bytes)
+    torch.cuda.synchronize()
+    return to_np(u), inv.cpu().numpy().astype(np.int64), nu
+
+
+def compare(keys, n_bits, n_ones, index_bytes=4):
+    u, inv, nu = gpu_dedup(keys, n_bits, n_ones, index_bytes)
+    ou, oinv = O.dedup(keys)
+    assert nu == ou.shape[0]
+    assert np.array_equal(u, ou)
+    assert np.array_equal(inv, oinv)
+
+
+def coupled_keys(name, n, eps=None):
+    s = synth.config_system(name)
+    off, td, hv = O.OracleSystem.of(s).gen(s.dets[:n], s.eps if eps is None else eps)
+    return s, td
+
+
+def test_tiny_coupled_set_rank_keys():
+    s, td = coupled_keys("tiny", 4900)
+    compare(td, 2 * s.norb, s.n_alpha + s.n_beta)
+
+
+def test_mid_coupled_set_rank_and_raw_keys():
+    s, td = coupled_keys("mid", 300)
+    compare(td, 2 * s.norb, s.n_alpha + s.n_beta)       # combinatorial-rank path
+    compare(td, 2 * s.norb, -1)                         # raw-bits path
+    compare(td, 2 * s.norb, s.n_alpha + s.n_beta, index_bytes=8)
+
+
+def test_two_word_keys():
+    s, td = coupled_keys("large", 2)
+    compare(td, 2 * s.norb, s.n_alpha + s.n_beta)       # C(120,20) > 2^64: raw 120-bit path
+    # 100 spin orbitals, 16 electrons: rank fits 64 bits although keys use 2 words
+    norb = 50
+    h1, h2 = synth.integrals(norb, seed=1)
+    dets = synth.sample_dets(norb, 8, 8, 300, seed=2)
+    off, td2, hv = O.OracleSystem(norb, 8, 8, h1, h2).gen(dets, 1e-8)
+    compare(td2, 2 * norb, 16)
+
+
+def test_edge_cases():
+    one = np.array([[5]], dtype=np.uint64)
+    compare(one, 3, 2)
+    same = np.full((10000, 1), 0b1011, dtype=np.uint64)
+    compare(same, 4, 3)
+    rng = np.random.default_rng(0)
+    raw = rng.integers(0, 1 << 62, size=(12345, 1)).astype(np.uint64)
+    raw[::3] = raw[1::3][: raw[::3].shape[0]]
+    compare(raw, 64, -1)
+    raw2 = rng.integers(0, 1 << 62, size=(5000, 2)).astype(np.uint64)
+    raw2[::2, 1] = 7
+    compare(raw2, 128, -1)
+    # empty
+    u, inv, nu = gpu_dedup(np.zeros((0, 1), dtype=np.uint64), 8, 2)
+    assert nu == 0
+
+
+def test_declared_popcount_violation_is_reported():
+    keys = np.array([[0b0111], [0b0011]], dtype=np.uint64)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cusci.dedup(to_dev(keys), 4, 3, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 1
+
+
+def test_workspace_too_small_is_an_error():
+    keys = to_dev(np.arange(1, 100, dtype=np.uint64).reshape(-1, 1))
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(cusci.CusciError):
+        # pass an explicit undersized workspace through the raw call
+        lib = cusci.load()
+        import ctypes
+        u = torch.empty_like(keys)
+        inv = torch.empty(keys.shape[0], dtype=torch.int32, device="cuda")
+        nu = torch.zeros(1, dtype=torch.int64, device="cuda")
+        rc = lib.cusci_dedup(ctypes.c_void_p(keys.data_ptr()), keys.shape[0], 1, 8, -1,
+                             ctypes.c_void_p(ws.data_ptr()), 16, ctypes.c_void_p(u.data_ptr()),
+                             ctypes.c_void_p(inv.data_ptr()), 4, ctypes.c_void_p(nu.data_ptr()),
+                             None, None, None)
+        cusci._check(rc, "cusci_dedup")
