@@ -1,0 +1,421 @@
+"""Benchmark of the coupled-configuration hot path on GB300.
+
+One step = count -> scan -> fill -> de-duplicate over one batch of sources of the
+mid-size system (52 spin orbitals, 7 alpha + 7 beta electrons, 100k sources
+drawn as random excitations of rank <= 4 out of the aufbau determinant,
+eps = 1e-8).  The metric is entries per second: coupled entries surviving the
+screening (diagonal included) generated and de-duplicated per second.  The
+energy forward + adjoint over a 200k selected set of the same system is timed
+beside it and reported as ``energy_fwd_bwd_ms``.
+
+``--impl reference`` times the CPU oracle instead, on a bounded sample of the
+same workload, on this host's cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the path is not sharded), the time is the maximum over ranks and the value the
+sum of all ranks' entries over that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled configs (+H_ij) generated & deduped per sec; % HBM roofline; energy+grad ms"
+UNIT = "entries/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None or not os.path.exists(self.path):
+            out["reasons"] = ["nvidia-smi unavailable"]
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle on a bounded sample of the workload (this host's cores)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2604_15768_gb300 import synth
+    s = synth.config_system("mid", n_dets=args.ref_sources)
+    osys = O.OracleSystem.of(s)
+    times, entries = [], 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        counts = osys.count(s.dets, s.eps)
+        off, td, hv = osys.gen(s.dets, s.eps, counts)
+        u, inv = O.dedup(td)
+        dt = time.perf_counter() - t0
+        entries = int(off[-1])
+        if it >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    value = entries / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "mid: 52 spin orbitals, 7a+7b, eps 1e-8, first "
+                               f"{args.ref_sources} of the 100k sources (bounded CPU sample)",
+                   "sources": args.ref_sources, "entries_per_step": entries},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                         "sample": f"first {args.ref_sources} sources of the 100k-source mid "
+                                   "workload, count+gen+dedup"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from paper_2604_15768_gb300 import cusci, synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    hbm_peak, peak_kind = _peaks()
+
+    s = synth.config_system("mid", n_dets=args.sources)
+    sysd = cusci.System.of(s)
+    n, W = s.dets.shape
+    n_bits, n_ones = 2 * s.norb, s.n_alpha + s.n_beta
+    d_src = cusci.dets_to_device(s.dets, dev)
+    stream = torch.cuda.current_stream()
+
+    # sizes from one untimed pass
+    counts = cusci.count_coupled(sysd, d_src, s.eps)
+    offsets = cusci.exclusive_scan(counts)
+    total = int(offsets[-1].item())
+    idx_bytes = 4 if total < 2 ** 31 else 8
+    out_d = torch.empty((total, W), dtype=torch.int64, device=dev)
+    out_h = torch.empty(total, dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    scan_ws = torch.empty(cusci.scan_workspace(n), dtype=torch.uint8, device=dev)
+    dd_ws = torch.empty(cusci.dedup_workspace(total, W, n_bits, n_ones), dtype=torch.uint8,
+                        device=dev)
+    uniq = torch.empty((total, W), dtype=torch.int64, device=dev)
+    inv = torch.empty(total, dtype=torch.int32 if idx_bytes == 4 else torch.int64, device=dev)
+    d_nu = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(marks=None):
+        m = marks or [None] * 4
+        cusci.count_coupled(sysd, d_src, s.eps, out=counts)
+        cusci.exclusive_scan(counts, out=offsets, workspace=scan_ws)
+        if m[1] is not None:
+            m[1].record(stream)
+        cusci.gen_coupled(sysd, d_src, s.eps, offsets, total, out_dets=out_d, out_h=out_h,
+                          status=status)
+        if m[2] is not None:
+            m[2].record(stream)
+        cusci.dedup_into(out_d, n_bits, n_ones, uniq, inv, d_nu, dd_ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_unique = int(d_nu.item())
+    assert int(status.item()) == 0, "fill pass reported inconsistent offsets"
+
+    l0 = cusci.kernel_launches()
+    per_step, t_count, t_gen, t_dedup = [], [], [], []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()                               # L2 flush, outside the events
+            marks = [ev(), ev(), ev(), ev()]
+            marks[0].record(stream)
+            step(marks)
+            marks[3].record(stream)
+            per_step.append(marks)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = cusci.kernel_launches() - l0
+    for m in per_step:
+        t_count.append(m[0].elapsed_time(m[1]))
+        t_gen.append(m[1].elapsed_time(m[2]))
+        t_dedup.append(m[2].elapsed_time(m[3]))
+    step_ms = [a + b + c for a, b, c in zip(t_count, t_gen, t_dedup)]
+    ms = float(np.mean(step_ms))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = ws * total / (ms * 1e-3)
+
+    # algorithmic bytes (8W+8 written per entry by the fill, 8W read + inverse
+    # written per entry and 8W per distinct key by the dedup, 8W + 16 per source)
+    gen_bytes = total * (8 * W + 8) + n * (8 * W + 16)
+    dedup_bytes = total * (8 * W + idx_bytes) + n_unique * 8 * W
+    step_bytes = gen_bytes + dedup_bytes + n * 16
+    gen_ms, dedup_ms, count_ms = (float(np.mean(t_gen)), float(np.mean(t_dedup)),
+                                  float(np.mean(t_count)))
+    gen_gbs = gen_bytes / (gen_ms * 1e-3) / 1e9
+    dedup_gbs = dedup_bytes / (dedup_ms * 1e-3) / 1e9
+    dominant = "cusci_dedup" if dedup_ms >= gen_ms else "cusci_gen_coupled (fill_kernel)"
+    dom_gbs, dom_bytes, dom_ms = ((dedup_gbs, dedup_bytes, dedup_ms) if dedup_ms >= gen_ms
+                                  else (gen_gbs, gen_bytes, gen_ms))
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(args, s, sysd, dev) if args.e2e else None
+
+    # energy forward + adjoint on the 200k selected set
+    energy = run_energy(args, dev) if args.energy else None
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = run_cpu_baseline(args) if (rank == 0 and ws == 1 and args.cpu_baseline) else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+            "data": "synthetic",
+            "config": {"workload": "mid: 52 spin orbitals, 7a+7b electrons, "
+                                   f"{n} sources (random excitations of rank<=4), eps=1e-8",
+                       "sources": n, "entries_per_step": total, "unique_per_step": n_unique,
+                       "inverse_bytes": idx_bytes, "parallelism": f"replicas{ws}",
+                       "l2": "flushed between steps (256 MiB write outside the timed events); "
+                             "each step also moves >40 GB"},
+            "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": dom_gbs / hbm_peak, "traffic": None, "kernel": dominant,
+                         "algorithmic_bytes_per_launch": dom_bytes, "ms_per_launch": dom_ms,
+                         "peak_kind": f"{peak_kind} (copy, burst)"},
+            "step_roofline": {"algorithmic_bytes": step_bytes,
+                              "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                              "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak},
+            "phases_ms": {"count+scan": count_ms, "gen": gen_ms, "dedup": dedup_ms},
+            "phases_gbs": {"gen": gen_gbs, "dedup": dedup_gbs},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "wall_s_timed": wall,
+        }
+        if e2e is not None:
+            line["e2e"] = e2e
+        if energy is not None:
+            line["energy_fwd_bwd_ms"] = energy["fwd_bwd_ms"]
+            line["energy"] = energy
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, s, sysd, dev):
+    """Same metric through the public API with host buffers: pinned host sources
+    copied in, count/scan/fill/dedup, the step's result (total and distinct
+    counts) read back, every step."""
+    import torch
+
+    from paper_2604_15768_gb300 import cusci
+    host = torch.from_numpy(np.ascontiguousarray(s.dets).view(np.int64)).pin_memory()
+    n_bits, n_ones = 2 * s.norb, s.n_alpha + s.n_beta
+    res = torch.empty(2, dtype=torch.int64).pin_memory()
+    times, total = [], 0
+
+    def one():
+        d = host.to(dev, non_blocking=True)
+        off, od, oh, st = cusci.coupled(sysd, d, s.eps)
+        u, inv, d_nu = cusci.dedup(od, n_bits, n_ones, sync=False)
+        out = torch.stack([off[-1], d_nu[0]])
+        res.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return int(res[0])
+
+    for _ in range(2):
+        one()
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        total = one()
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    return {"value": total / t, "unit": UNIT, "h2d_bytes_per_step": int(host.numel() * 8),
+            "d2h_bytes_per_step": 16, "ms_per_step": t * 1e3,
+            "api": "cusci.coupled + cusci.dedup (host-pinned sources in, totals out)"}
+
+
+def mlp_psi(S_np, norb, dev):
+    """psi = exp(logamp) from a seeded MLP (occupation bits -> 256 -> 256 -> 1,
+    tanh, FP32 weights, FP64 output)."""
+    import torch
+    torch.manual_seed(0)
+    net = torch.nn.Sequential(torch.nn.Linear(2 * norb, 256), torch.nn.Tanh(),
+                              torch.nn.Linear(256, 256), torch.nn.Tanh(),
+                              torch.nn.Linear(256, 1)).to(dev)
+    bits = ((S_np[:, :1] >> np.arange(2 * norb, dtype=np.uint64)) & np.uint64(1)).astype(np.float32)
+    x = torch.from_numpy(bits).to(dev)
+    return net, x
+
+
+def run_energy(args, dev):
+    import torch
+
+    from paper_2604_15768_gb300 import cusci, synth
+    s = synth.config_system("energy", n_dets=args.energy_sources)
+    sysd = cusci.System.of(s)
+    dS = cusci.dets_to_device(s.dets, dev)
+    net, x = mlp_psi(s.dets, s.norb, dev)
+
+    def fwd_bwd():
+        psi = torch.exp(net(x).squeeze(-1).double())
+        E = cusci.Energy.apply(psi, sysd, dS, s.eps, False)
+        E.backward()
+        return E
+
+    for _ in range(2):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    # time only the library's forward and adjoint with events
+    psi = torch.exp(net(x).squeeze(-1).double()).detach()
+    ws_e = torch.empty(cusci.energy_workspace(sysd, dS.shape[0]), dtype=torch.uint8, device=dev)
+    fwd, bwd = [], []
+    for _ in range(3):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        E, n2, hp = cusci.energy_fwd(sysd, dS, psi, s.eps, workspace=ws_e)
+        b.record()
+        cusci.energy_bwd(sysd, dS, psi, s.eps, E, n2, hpsi=hp, workspace=ws_e)
+        c.record()
+        torch.cuda.synchronize()
+        fwd.append(a.elapsed_time(b))
+        bwd.append(b.elapsed_time(c))
+    return {"fwd_ms": float(np.median(fwd)), "bwd_ms": float(np.median(bwd)),
+            "fwd_bwd_ms": float(np.median(fwd) + np.median(bwd)), "E": float(E.item()),
+            "selected": int(dS.shape[0]),
+            "workload": "mid system, selected set of sorted distinct sampled dets, psi from a "
+                        "seeded 256-256 tanh MLP"}
+
+
+def run_cpu_baseline(args):
+    from oracle import oracle as O
+    from paper_2604_15768_gb300 import synth
+    s = synth.config_system("mid", n_dets=args.ref_sources)
+    osys = O.OracleSystem.of(s)
+    t0 = time.perf_counter()
+    counts = osys.count(s.dets, s.eps)
+    off, td, hv = osys.gen(s.dets, s.eps, counts)
+    O.dedup(td)
+    t = time.perf_counter() - t0
+    return {"value": int(off[-1]) / t, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"first {args.ref_sources} sources of the mid workload (count+gen+dedup, "
+                      f"{int(off[-1])} entries, {t:.1f} s)"}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sources", type=int, default=100_000)
+    ap.add_argument("--energy-sources", type=int, default=200_000)
+    ap.add_argument("--ref-sources", type=int, default=2000)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-energy", dest="energy", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

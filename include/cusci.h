@@ -71,6 +71,9 @@ typedef struct cusci_system cusci_system; /* opaque, library-owned */
 const char *cusci_last_error(void);
 /* Library version string. */
 const char *cusci_version(void);
+/* Number of kernels the library has launched in this process so far (host-side
+ * count of successful launches, all devices and streams). */
+uint64_t cusci_kernel_launches(void);
 
 /* ------------------------------------------------------------------ system
  * Builds the device-side integral tables of one molecular system (the
@@ -96,8 +99,8 @@ cusci_status cusci_count_coupled(const cusci_system *sys, const uint64_t *d_dets
                                  double eps, int64_t *d_counts, void *stream);
 
 /* Exclusive prefix sum: d_offsets[0] = 0, d_offsets[k+1] = d_offsets[k] +
- * d_counts[k] (device int64, n+1 entries).  d_total (device, nullable) receives
- * d_offsets[n].  Workspace: cusci_scan_workspace bytes of device memory. */
+ * d_counts[k] (device int64, n+1 entries, so d_offsets[n] is the total).
+ * Workspace: cusci_scan_workspace bytes of device memory, 8-byte aligned. */
 cusci_status cusci_scan_workspace(int64_t n, size_t *bytes);
 cusci_status cusci_exclusive_scan(const int64_t *d_counts, int64_t n, int64_t *d_offsets,
                                   void *d_ws, size_t ws_bytes, void *stream);

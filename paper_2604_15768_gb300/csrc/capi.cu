@@ -1,4 +1,5 @@
 // Error reporting and version of the C ABI.
+#include <atomic>
 #include <stdarg.h>
 #include <stdio.h>
 
@@ -6,9 +7,12 @@
 
 namespace {
 thread_local char g_last_error[512] = "";
+std::atomic<unsigned long long> g_launches{0};
 }
 
 namespace cusci {
+
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
 
 cusci_status fail(cusci_status st, const char *fmt, ...) {
     va_list ap;
@@ -27,3 +31,4 @@ cusci_status cuda_fail(cudaError_t e, const char *what) {
 
 extern "C" const char *cusci_last_error(void) { return g_last_error; }
 extern "C" const char *cusci_version(void) { return "cusci 0.1 (sm_103a)"; }
+extern "C" uint64_t cusci_kernel_launches(void) { return (uint64_t)g_launches.load(); }

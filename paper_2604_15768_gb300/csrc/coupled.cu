@@ -130,7 +130,7 @@ extern "C" cusci_status cusci_count_coupled(const cusci_system *sys, const uint6
         count_kernel<1><<<grid_for(n), 32 * WARPS_PER_BLOCK, 0, st>>>(v, d_dets, n, eps, d_counts);
     else
         count_kernel<2><<<grid_for(n), 32 * WARPS_PER_BLOCK, 0, st>>>(v, d_dets, n, eps, d_counts);
-    CUSCI_CHECK_LAUNCH("count_kernel");
+    CUSCI_LAUNCHED(1, "count_kernel");
     return CUSCI_OK;
 }
 
@@ -159,7 +159,7 @@ extern "C" cusci_status cusci_gen_coupled(const cusci_system *sys, const uint64_
     else
         fill_kernel<2><<<grid_for(n), 32 * WARPS_PER_BLOCK, 0, st>>>(
             v, d_dets, n, eps, d_offsets, d_out_dets, d_out_h, d_status);
-    CUSCI_CHECK_LAUNCH("fill_kernel");
+    CUSCI_LAUNCHED(1, "fill_kernel");
     return CUSCI_OK;
 }
 
@@ -173,6 +173,6 @@ extern "C" cusci_status cusci_check_dets(const cusci_system *sys, const uint64_t
     if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     check_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_dets, n, sys->W, sys->norb,
                                                            sys->n_alpha, sys->n_beta, d_status);
-    CUSCI_CHECK_LAUNCH("check_kernel");
+    CUSCI_LAUNCHED(1, "check_kernel");
     return CUSCI_OK;
 }

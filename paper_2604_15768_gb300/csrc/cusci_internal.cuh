@@ -42,6 +42,9 @@ struct cusci_system {
 
 namespace cusci {
 
+// number of kernel launches issued by the library (capi.cu)
+void note_launches(int n);
+
 // thread-local error message plumbing (capi.cu)
 cusci_status fail(cusci_status st, const char *fmt, ...);
 cusci_status cuda_fail(cudaError_t e, const char *what);
@@ -88,4 +91,11 @@ inline int sm_count() {
     do {                                                          \
         cudaError_t _e = cudaGetLastError();                      \
         if (_e != cudaSuccess) return cusci::cuda_fail(_e, what); \
+    } while (0)
+
+// launches `n` kernels' worth of bookkeeping, then checks the launch status
+#define CUSCI_LAUNCHED(n, what)   \
+    do {                          \
+        cusci::note_launches(n);  \
+        CUSCI_CHECK_LAUNCH(what); \
     } while (0)

@@ -423,7 +423,7 @@ cusci_status run_dedup(const Plan &p, const uint64_t *d_keys, int64_t total, int
 
     prepare_keys<W, KW><<<ew_blocks, 256, 0, st>>>(d_keys, total, n_bits, n_ones, p.mode, k0, i0,
                                                     d_status);
-    CUSCI_CHECK_LAUNCH("dedup prepare");
+    CUSCI_LAUNCHED(1, "dedup prepare");
     const size_t smem = sizeof(DownSmem<KW>);
     static bool attr_set[3] = {false, false, false};
     if (!attr_set[KW]) {
@@ -441,7 +441,7 @@ cusci_status run_dedup(const Plan &p, const uint64_t *d_keys, int64_t total, int
         cusci_status rc = exclusive_scan_i64(base, nh, base, scanws, st);
         if (rc != CUSCI_OK) return rc;
         downsweep<KW><<<p.grid, RT, smem, st>>>(k0, i0, k1, i1, total, shift, p.per_cta, base);
-        CUSCI_CHECK_LAUNCH("dedup radix pass");
+        CUSCI_LAUNCHED(3, "dedup radix pass");
         Key<KW> *tk = k0; k0 = k1; k1 = tk;
         uint32_t *ti = i0; i0 = i1; i1 = ti;
     }
@@ -452,7 +452,7 @@ cusci_status run_dedup(const Plan &p, const uint64_t *d_keys, int64_t total, int
     unique_scatter<KW, W><<<(unsigned)ut, UT, 0, st>>>(k0, i0, total, tileoff, p.mode, n_bits,
                                                        n_ones, d_unique, d_inverse, index_bytes,
                                                        d_n_unique);
-    CUSCI_CHECK_LAUNCH("dedup unique");
+    CUSCI_LAUNCHED(2, "dedup unique");
     return CUSCI_OK;
 }
 

@@ -225,7 +225,7 @@ cusci_status compute_hpsi(const cusci_system *sys, const uint64_t *d_S, int64_t 
         insert_S<2><<<ib, 256, 0, st>>>(tb, d_S, nS, d_status);
         hpsi_kernel<2><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp);
     }
-    CUSCI_CHECK_LAUNCH("energy: H psi");
+    CUSCI_LAUNCHED(2, "energy: H psi");
     return CUSCI_OK;
 }
 
@@ -254,7 +254,7 @@ extern "C" cusci_status cusci_energy_fwd(const cusci_system *sys, const uint64_t
     cusci_status rc = compute_hpsi(sys, d_S, nS, d_psi, eps, hp, d_ws, ws_bytes, d_status, st);
     if (rc != CUSCI_OK) return rc;
     reduce_energy<<<1, RED_T, 0, st>>>(d_psi, hp, nS, d_E, d_norm2);
-    CUSCI_CHECK_LAUNCH("energy: reduction");
+    CUSCI_LAUNCHED(1, "energy: reduction");
     return CUSCI_OK;
 }
 
@@ -277,6 +277,6 @@ extern "C" cusci_status cusci_energy_bwd(const cusci_system *sys, const uint64_t
     int blocks = (int)((nS + 255) / 256);
     if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     grad_kernel<<<blocks, 256, 0, st>>>(d_psi, hp, nS, d_E, d_norm2, d_grad_out, d_grad);
-    CUSCI_CHECK_LAUNCH("energy: gradient");
+    CUSCI_LAUNCHED(1, "energy: gradient");
     return CUSCI_OK;
 }

@@ -117,7 +117,7 @@ cusci_status exclusive_scan_i64(const int64_t *in, int64_t n, int64_t *out, int6
     tile_sums<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(in, n, ws);
     scan_sums<<<1, SCAN_THREADS, 0, st>>>(ws, nt);
     tile_scan<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(in, n, ws, nt, out);
-    CUSCI_CHECK_LAUNCH("exclusive scan");
+    CUSCI_LAUNCHED(3, "exclusive scan");
     return CUSCI_OK;
 }
 

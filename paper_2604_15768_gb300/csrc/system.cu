@@ -112,7 +112,7 @@ cusci_status masks_for(cusci_system *sys, double eps, cudaStream_t stream, const
     int blocks = (int)((rows + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     build_masks<<<blocks, 256, 0, stream>>>(n, sys->T, eps, m.bits);
-    CUSCI_CHECK_LAUNCH("build_masks");
+    CUSCI_LAUNCHED(1, "build_masks");
     m.eps = eps;
     m.valid = true;
     m.stamp = ++sys->clock;

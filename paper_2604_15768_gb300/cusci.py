@@ -42,6 +42,7 @@ class CusciError(RuntimeError):
 _PROTOS = {
     "cusci_last_error": (ctypes.c_char_p, []),
     "cusci_version": (ctypes.c_char_p, []),
+    "cusci_kernel_launches": (ctypes.c_uint64, []),
     "cusci_system_create": (_I, [_I, _I, _I, _P, _P, _D, ctypes.POINTER(_P)]),
     "cusci_system_destroy": (None, [_P]),
     "cusci_system_words": (_I, [_P]),
@@ -77,6 +78,11 @@ def load(path: str | None = None):
                 fn.argtypes = args
             _LIB = lib
     return _LIB
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libcusci in this process so far."""
+    return int(load().cusci_kernel_launches())
 
 
 def _check(rc: int, where: str):
@@ -161,16 +167,22 @@ def count_coupled(sys: System, dets: torch.Tensor, eps: float, out=None, stream=
     return out
 
 
-def exclusive_scan(counts: torch.Tensor, out=None, stream=None):
+def scan_workspace(n: int) -> int:
+    ws = ctypes.c_size_t()
+    _check(load().cusci_scan_workspace(int(n), ctypes.byref(ws)), "cusci_scan_workspace")
+    return max(1, ws.value)
+
+
+def exclusive_scan(counts: torch.Tensor, out=None, workspace=None, stream=None):
     counts = _dev(counts, torch.int64, "counts")
     n = counts.shape[0]
-    lib = load()
-    ws = ctypes.c_size_t()
-    _check(lib.cusci_scan_workspace(n, ctypes.byref(ws)), "cusci_scan_workspace")
-    wbuf = torch.empty(max(1, ws.value), dtype=torch.uint8, device=counts.device)
+    need = scan_workspace(n)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=counts.device)
     out = out if out is not None else torch.empty(n + 1, dtype=torch.int64, device=counts.device)
-    _check(lib.cusci_exclusive_scan(_ptr(counts), n, _ptr(out), _ptr(wbuf), ws.value,
-                                    _stream(stream)), "cusci_exclusive_scan")
+    _check(load().cusci_exclusive_scan(_ptr(counts), n, _ptr(out), _ptr(workspace),
+                                       workspace.numel(), _stream(stream)),
+           "cusci_exclusive_scan")
     return out
 
 
@@ -225,6 +237,17 @@ def dedup(keys: torch.Tensor, n_bits: int, n_ones: int = -1, index_bytes: int = 
     if sync:
         return unique[:h_nu.value], inverse[:total], h_nu.value
     return unique, inverse[:total], d_nu
+
+
+def dedup_into(keys: torch.Tensor, n_bits: int, n_ones: int, unique: torch.Tensor,
+               inverse: torch.Tensor, n_unique: torch.Tensor, workspace: torch.Tensor,
+               status=None, stream=None):
+    """Asynchronous de-duplication into caller-owned buffers (no host sync)."""
+    total, W = keys.shape
+    ib = 4 if inverse.dtype == torch.int32 else 8
+    _check(load().cusci_dedup(_ptr(keys), total, W, int(n_bits), int(n_ones), _ptr(workspace),
+                              workspace.numel(), _ptr(unique), _ptr(inverse), ib, _ptr(n_unique),
+                              None, _ptr(status), _stream(stream)), "cusci_dedup")
 
 
 def coupled(sys: System, dets: torch.Tensor, eps: float, stream=None):
