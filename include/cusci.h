@@ -105,6 +105,24 @@ cusci_status cusci_scan_workspace(int64_t n, size_t *bytes);
 cusci_status cusci_exclusive_scan(const int64_t *d_counts, int64_t n, int64_t *d_offsets,
                                   void *d_ws, size_t ws_bytes, void *stream);
 
+/* Exclusive prefix sum that allocates nothing.  The paper has no counterpart;
+ * it exists for callers that cannot allocate device memory or pass a
+ * workspace: code inside a framework that has reserved the device's memory for
+ * its own pool, latency-critical loops where cudaMalloc's implicit device
+ * synchronisation would stall other streams, and bindings that can only pass
+ * pointers to existing buffers.  Same result as cusci_exclusive_scan.
+ * Scratch: a fixed array inside the library (512 KiB per device, held by every
+ * device that loads the library until the process exits); n is limited to
+ * cusci_scan_static_max() counts (134,217,728), larger n returns
+ * CUSCI_ERR_UNSUPPORTED.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current), so make that
+ * first call before any stream capture.  All calls share the one array: calls
+ * that overlap on the GPU (other streams, other threads) race and must be
+ * ordered by the caller.  Calls no cudaMalloc, cudaFree or allocating routine. */
+int64_t cusci_scan_static_max(void);
+cusci_status cusci_exclusive_scan_static(const int64_t *d_counts, int64_t n, int64_t *d_offsets,
+                                         void *stream);
+
 /* Fill pass (Algorithm 1 and Sec. 4.2.2): writes C_i to rows
  * [d_offsets[i], d_offsets[i+1]) of d_out_dets (device [total][W]) and d_out_h
  * (device double[total]) in canonical order.  d_offsets must be the exclusive

@@ -3,6 +3,8 @@
 // Three phases over tiles of 2048 elements: tile sums, one-block scan of the
 // tile sums, tile-local scans plus the tile prefix.
 
+#include <mutex>
+
 #include "cusci_internal.cuh"
 
 namespace cusci {
@@ -143,4 +145,73 @@ extern "C" cusci_status cusci_exclusive_scan(const int64_t *d_counts, int64_t n,
     if (((uintptr_t)d_ws & 7u) || ((uintptr_t)d_offsets & 7u) || ((uintptr_t)d_counts & 7u))
         return fail(CUSCI_ERR_INVALID, "cusci_exclusive_scan: buffers must be 8-byte aligned");
     return exclusive_scan_i64(d_counts, n, d_offsets, (int64_t *)d_ws, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan without allocation.
+//
+// The tile sums of the scan above normally live in a caller-provided
+// workspace.  Some callers cannot hand one over: code running inside a
+// framework that has reserved the device's memory for its own pool, code in a
+// latency-critical loop where cudaMalloc's implicit device-wide
+// synchronisation would stall other streams, and bindings that can only pass
+// the pointers of existing buffers.  For them the scratch lives in the
+// fixed-size array below, which every device that loads this library holds
+// until the process exits (CUSCI_SCAN_STATIC_TILES + 1 int64, 512 KiB + 8 B).
+// In host code `g_scan_static` names a host-side shadow, not device memory, so
+// its device address is looked up once per device with cudaGetSymbolAddress.
+
+namespace cusci {
+namespace {
+
+constexpr int64_t CUSCI_SCAN_STATIC_TILES = 65536;   // => n <= 65536 * 2048 counts
+static __device__ __align__(256) int64_t g_scan_static[CUSCI_SCAN_STATIC_TILES + 1];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_static_mu;
+int64_t *g_static_ptr[MAX_DEVICES] = {nullptr};
+
+cusci_status static_scratch(int64_t **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cusci_exclusive_scan_static: cudaGetDevice");
+    if (dev < 0 || dev >= MAX_DEVICES)
+        return fail(CUSCI_ERR_UNSUPPORTED, "cusci_exclusive_scan_static: device %d >= %d", dev,
+                    MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scan_static);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cusci_exclusive_scan_static: cudaGetSymbolAddress");
+        g_static_ptr[dev] = (int64_t *)p;
+    }
+    *out = g_static_ptr[dev];
+    return CUSCI_OK;
+}
+
+}  // namespace
+}  // namespace cusci
+
+extern "C" int64_t cusci_scan_static_max(void) {
+    return cusci::CUSCI_SCAN_STATIC_TILES * cusci::SCAN_TILE;
+}
+
+extern "C" cusci_status cusci_exclusive_scan_static(const int64_t *d_counts, int64_t n,
+                                                    int64_t *d_offsets, void *stream) {
+    using namespace cusci;
+    if (n < 0 || !d_offsets || (n > 0 && !d_counts))
+        return fail(CUSCI_ERR_INVALID, "cusci_exclusive_scan_static: bad argument");
+    if (n > CUSCI_SCAN_STATIC_TILES * SCAN_TILE)
+        return fail(CUSCI_ERR_UNSUPPORTED,
+                    "cusci_exclusive_scan_static: n=%lld exceeds the static scratch limit of "
+                    "%lld counts; use cusci_exclusive_scan with a workspace",
+                    (long long)n, (long long)(CUSCI_SCAN_STATIC_TILES * SCAN_TILE));
+    if (((uintptr_t)d_offsets & 7u) || ((uintptr_t)d_counts & 7u))
+        return fail(CUSCI_ERR_INVALID, "cusci_exclusive_scan_static: buffers must be 8-byte aligned");
+    int64_t *scratch = nullptr;
+    cusci_status rc = static_scratch(&scratch);
+    if (rc != CUSCI_OK) return rc;
+    // every tile sum is written before it is read, so nothing needs clearing
+    return exclusive_scan_i64(d_counts, n, d_offsets, scratch, (cudaStream_t)stream);
 }

@@ -49,6 +49,8 @@ _PROTOS = {
     "cusci_count_coupled": (_I, [_P, _P, _I64, _D, _P, _P]),
     "cusci_scan_workspace": (_I, [_I64, ctypes.POINTER(_SZ)]),
     "cusci_exclusive_scan": (_I, [_P, _I64, _P, _P, _SZ, _P]),
+    "cusci_scan_static_max": (_I64, []),
+    "cusci_exclusive_scan_static": (_I, [_P, _I64, _P, _P]),
     "cusci_gen_coupled": (_I, [_P, _P, _I64, _D, _P, _P, _P, _P, _P]),
     "cusci_check_dets": (_I, [_P, _P, _I64, _P, _P]),
     "cusci_dedup_workspace": (_I, [_I64, _I, _I, _I, ctypes.POINTER(_SZ)]),
