@@ -61,12 +61,20 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK)
     }
 }
 
-template <int W>
+template <int W, bool STAGE>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK)
     fill_kernel(SysView v, const uint64_t *__restrict__ dets, int64_t n, double eps,
                 const int64_t *__restrict__ offsets, uint64_t *__restrict__ out_d,
                 double *__restrict__ out_h, int32_t *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
+    WarpStage st;
+    WarpStage *stp = nullptr;
+    if (STAGE) {
+        stage_init(st, smem + (threadIdx.x >> 5) * stage_bytes(v.slab, v.mrow), v.slab, v.mrow,
+                   lane, status);
+        stp = &st;
+    }
     const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
     for (int64_t src = warp; src < n; src += nwarps) {
@@ -76,7 +84,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK)
         bool ok = end >= beg;
         if (ok) {
             FillEmit<W> em{out_d, out_h, beg, end};
-            ok = visit_source<W>(v, s, eps, lane, em) == end - beg;
+            ok = visit_source<W>(v, s, eps, lane, em, stp) == end - beg;
         }
         if (!ok && lane == 0 && status) *status = CUSCI_ERR_OVERFLOW;
     }
@@ -102,10 +110,39 @@ __global__ void check_kernel(const uint64_t *__restrict__ dets, int64_t n, int W
     }
 }
 
-int grid_for(int64_t n) {
+int grid_for(int64_t n, int per_sm = 8) {
     int64_t want = (n + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-    int64_t cap = (int64_t)sm_count() * 8;
+    int64_t cap = (int64_t)sm_count() * per_sm;
     return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+// fill launch: staged integral slabs in shared memory when they fit
+template <int W>
+cusci_status launch_fill(const SysView &v, const uint64_t *d_dets, int64_t n, double eps,
+                         const int64_t *d_offsets, uint64_t *d_out_dets, double *d_out_h,
+                         int32_t *d_status, cudaStream_t st) {
+    const size_t smem = (size_t)WARPS_PER_BLOCK * stage_bytes(v.slab, v.mrow);
+    if (W == 1 && smem <= 200 * 1024) {
+        static size_t attr = 0;
+        if (attr < smem) {
+            cudaError_t e = cudaFuncSetAttribute(fill_kernel<W, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e, "fill: shared-memory attribute");
+            attr = smem;
+        }
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, fill_kernel<W, true>, 32 * WARPS_PER_BLOCK, smem);
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        fill_kernel<W, true><<<grid_for(n, per_sm), 32 * WARPS_PER_BLOCK, smem, st>>>(
+            v, d_dets, n, eps, d_offsets, d_out_dets, d_out_h, d_status);
+    } else {
+        fill_kernel<W, false><<<grid_for(n), 32 * WARPS_PER_BLOCK, 0, st>>>(
+            v, d_dets, n, eps, d_offsets, d_out_dets, d_out_h, d_status);
+    }
+    CUSCI_LAUNCHED(1, "fill_kernel");
+    return CUSCI_OK;
 }
 
 }  // namespace
@@ -154,13 +191,8 @@ extern "C" cusci_status cusci_gen_coupled(const cusci_system *sys, const uint64_
     if (rc != CUSCI_OK) return rc;
     SysView v = view_of(sys, mask);
     if (sys->W == 1)
-        fill_kernel<1><<<grid_for(n), 32 * WARPS_PER_BLOCK, 0, st>>>(
-            v, d_dets, n, eps, d_offsets, d_out_dets, d_out_h, d_status);
-    else
-        fill_kernel<2><<<grid_for(n), 32 * WARPS_PER_BLOCK, 0, st>>>(
-            v, d_dets, n, eps, d_offsets, d_out_dets, d_out_h, d_status);
-    CUSCI_LAUNCHED(1, "fill_kernel");
-    return CUSCI_OK;
+        return launch_fill<1>(v, d_dets, n, eps, d_offsets, d_out_dets, d_out_h, d_status, st);
+    return launch_fill<2>(v, d_dets, n, eps, d_offsets, d_out_dets, d_out_h, d_status, st);
 }
 
 extern "C" cusci_status cusci_check_dets(const cusci_system *sys, const uint64_t *d_dets,

@@ -12,7 +12,7 @@
 namespace cusci {
 
 // One cached set of screening bitmasks for a given eps.
-// bits[((kind*norb + pi)*norb + pj)*norb + pa] has bit pb set iff the double
+// bits[((kind*norb + pi)*norb + pj)*mrow + pa] has bit pb set iff the double
 // excitation with spatial occupied (pi, pj) and virtual (pa, pb) survives
 // |H| > eps; kind 0 = both electrons of one spin (only pi < pj, pa < pb are
 // set), kind 1 = opposite spins.
@@ -35,7 +35,10 @@ struct cusci_system {
     double *K;    // [p][q] = (pq|qp)
     double *S1;   // [pa][pi][pk] = (pa pi|pk pk)
     double *S2;   // [pa][pi][pk] = (pa pk|pk pi)
-    double *T;    // [kind][pi][pj][pa][pb]: kind 0 (ai|bj)-(aj|bi), kind 1 (ai|bj)
+    double *T;    // [kind][pi][pj] slabs of `slab` doubles, element [pa*norb + pb]:
+                  // kind 0 (ai|bj)-(aj|bi), kind 1 (ai|bj)
+    int slab;     // norb^2 rounded up to even (16-byte slabs for bulk copies)
+    int mrow;     // norb rounded up to even (16-byte mask rows)
     cusci::MaskSlot masks[CUSCI_MASK_SLOTS];
     uint64_t clock;
 };
@@ -55,7 +58,7 @@ cusci_status masks_for(cusci_system *sys, double eps, cudaStream_t stream,
 
 // device view of a system for kernels
 struct SysView {
-    int norb, M, W;
+    int norb, M, W, slab, mrow;
     double ecore;
     const double *__restrict__ h1;
     const double *__restrict__ J;
@@ -69,6 +72,7 @@ struct SysView {
 inline SysView view_of(const cusci_system *s, const uint64_t *mask) {
     SysView v;
     v.norb = s->norb; v.M = s->M; v.W = s->W; v.ecore = s->ecore;
+    v.slab = s->slab; v.mrow = s->mrow;
     v.h1 = s->h1; v.J = s->J; v.K = s->K; v.S1 = s->S1; v.S2 = s->S2; v.T = s->T;
     v.mask = mask;
     return v;

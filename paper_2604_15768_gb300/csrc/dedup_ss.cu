@@ -1,0 +1,903 @@
+// Sample-sort de-duplication: the paper's regular-sampling de-duplication
+// (Sec. 4.1.1, Fig. 3) re-thought for one GB300, with the thread blocks of one
+// GPU in the role of the paper's ranks.
+//
+//  1. Regular sampling: OVS samples per leaf bucket are taken at fixed strides
+//     of the input, sorted, and every OVS-th sample becomes a splitter
+//     (Step 1 and Step 2 of Sec. 4.1.1).  Equal keys always fall into the same
+//     bucket; the skewed key distribution (configurations near the reference
+//     determinant are far more frequent) is balanced by the sample, not by the
+//     key bits.
+//  2. Partition in two levels instead of the all-to-all exchange (Step 3): a
+//     4096-way split by the level-1 splitters, then a 128-way split of every
+//     level-1 bucket, giving ~524k leaf buckets of ~3k entries.  Each
+//     partition pass is a contiguous-chunk scatter whose per-block write
+//     fronts (4096 buckets x 304 blocks x 32 B = 40 MB) stay inside the
+//     129 MB L2, so DRAM sees whole sectors.  Slots inside a bucket are handed
+//     out with warp-aggregated shared-memory atomics; the slot of every entry
+//     is kept (4 B) so the reverse index can be gathered back later.
+//  3. Each leaf is loaded into shared memory, packed as
+//     (key - leaf_min) << pos_bits | position, LSD radix-sorted there (stable
+//     8-bit passes over the key bits only), and walked once to mark run heads:
+//     the local unique id of every position and the distinct keys.
+//  4. A scan of per-leaf distinct counts gives the global unique ids; the
+//     distinct keys are compacted (un-ranked back to determinants), and the
+//     reverse index is gathered back through the two stored slot arrays --
+//     reads with the same L2 locality as the scatters, instead of a random
+//     4-byte scatter per entry into the reverse index.
+// Single-word keys are compared as they are; two-word keys by their rank in the
+// combinatorial number system (order preserving for a fixed number of
+// electrons) when it fits 42 bits; other inputs take the LSD path in dedup.cu.
+// A leaf whose packed form would not fit 64 bits, or that exceeds the
+// shared-memory capacity, is sorted in global memory with its positions in a
+// separate array.
+
+#include <string.h>
+
+#include "radix.cuh"
+
+namespace cusci {
+cusci_status exclusive_scan_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *ws,
+                                cudaStream_t st);
+int64_t scan_tiles(int64_t n);
+
+namespace ss {
+
+constexpr int T = 256;
+constexpr int WARPS = T / 32;
+constexpr int B2 = 256;
+constexpr int LOG2_B2 = 8;
+constexpr int OVS = 4;
+constexpr int LEAF_CAP = 4096;
+constexpr int LEAF_AVG = 1600;
+constexpr int MAX_B1 = 4096;
+constexpr int BT_MAX = 2048;      // binomial-table entries staged in shared memory
+constexpr int LRI = 8;            // leaf ranking: entries per thread per tile
+constexpr int LTILE = T * LRI;    // 2048
+constexpr int MAX_KEY_BITS = 42;   // rank keys: packed with up to 22 position bits
+constexpr int MAX_RAW_BITS = 64;   // raw single-word keys
+constexpr unsigned FULL = 0xffffffffu;
+
+struct Plan {
+    int64_t N;
+    int W, n_bits, n_ones, mode, key_bits, kcols;
+    int B1, log2B1;
+    int64_t NL, NS;
+    int G;
+    int64_t per_cta;
+    int gs;          // grid of the sample sort
+    int64_t gs_per;  // per-CTA range of the sample sort
+    int s_passes;
+    size_t o_bt, o_samp, o_samp2, o_sidx, o_sidx2, o_shist, o_sbase, o_scanws, o_LS, o_H1,
+        o_base1, o_bid1, o_K1, o_dest1, o_bid2, o_K2, o_dest2, o_U2, o_tmpU, o_leafst, o_ucnt,
+        o_ubase, o_pay, o_kbase, bytes;
+};
+
+unsigned __int128 binom128(int m, int k) {
+    if (k < 0 || k > m) return 0;
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; i++) {
+        r = r * (unsigned)(m - k + i) / (unsigned)i;
+        if (r > ((unsigned __int128)1 << 100)) return (unsigned __int128)1 << 100;
+    }
+    return r;
+}
+
+int bitlen128(unsigned __int128 x) {
+    int b = 0;
+    while (x) { b++; x >>= 1; }
+    return b;
+}
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool eligible(int64_t N, int W, int n_bits, int n_ones, int *mode, int *key_bits) {
+    if (N < ((int64_t)1 << 22) || N >= ((int64_t)1 << 32)) return false;
+    if (W == 1 && n_bits <= MAX_RAW_BITS) { *mode = 0; *key_bits = n_bits; return true; }
+    if (n_ones >= 0 && n_ones < 64 && n_bits * (n_ones + 1) <= BT_MAX) {
+        const unsigned __int128 space = binom128(n_bits, n_ones);
+        const int kb = space > 1 ? bitlen128(space - 1) : 1;
+        if (kb <= MAX_KEY_BITS) { *mode = 1; *key_bits = kb; return true; }
+    }
+    return false;
+}
+
+Plan make_plan(int64_t N, int W, int n_bits, int n_ones, int mode, int key_bits) {
+    Plan p;
+    memset(&p, 0, sizeof(p));
+    p.N = N; p.W = W; p.n_bits = n_bits; p.n_ones = n_ones; p.mode = mode;
+    p.key_bits = key_bits;
+    p.kcols = mode == 1 ? n_ones + 1 : 1;
+    const int64_t want_leaves = (N + LEAF_AVG - 1) / LEAF_AVG;
+    int64_t b1 = (want_leaves + B2 - 1) / B2;
+    p.B1 = 1; p.log2B1 = 0;
+    while (p.B1 < b1 && p.B1 < MAX_B1) { p.B1 <<= 1; p.log2B1++; }
+    p.NL = (int64_t)p.B1 * B2;
+    p.NS = p.NL * OVS;
+    if (p.NS > N) p.NS = N;
+    p.G = sm_count() * 2;
+    p.per_cta = ((N + p.G - 1) / p.G + 31) / 32 * 32;
+    // sample sort grid (radix building blocks)
+    const int64_t tiles = (p.NS + radix::RTILE - 1) / radix::RTILE;
+    int64_t gs = sm_count();
+    if (gs > tiles) gs = tiles;
+    if (gs < 1) gs = 1;
+    const int64_t tpc = (tiles + gs - 1) / gs;
+    p.gs_per = tpc * radix::RTILE;
+    p.gs = (int)((p.NS + p.gs_per - 1) / p.gs_per);
+    p.s_passes = (key_bits + radix::RBITS - 1) / radix::RBITS;
+    size_t o = 0;
+    p.o_bt = o; o = al(o + BT_MAX * 8);
+    p.o_samp = o; o = al(o + p.NS * 8);
+    p.o_samp2 = o; o = al(o + p.NS * 8);
+    p.o_sidx = o; o = al(o + p.NS * 4);
+    p.o_sidx2 = o; o = al(o + p.NS * 4);
+    p.o_shist = o; o = al(o + (size_t)radix::RADIX * p.gs * 4);
+    p.o_sbase = o; o = al(o + ((size_t)radix::RADIX * p.gs + 1) * 8);
+    int64_t scan_n = (int64_t)p.B1 * p.G;
+    if (p.NL > scan_n) scan_n = p.NL;
+    if ((int64_t)radix::RADIX * p.gs > scan_n) scan_n = (int64_t)radix::RADIX * p.gs;
+    p.o_scanws = o; o = al(o + (scan_tiles(scan_n) + 2) * 8);
+    p.o_LS = o; o = al(o + p.NL * 8);
+    p.o_H1 = o; o = al(o + (size_t)p.B1 * p.G * 4);
+    p.o_base1 = o; o = al(o + ((size_t)p.B1 * p.G + 1) * 8);
+    p.o_bid1 = o; o = al(o + N * 2);
+    p.o_K1 = o; o = al(o + N * 8);
+    p.o_dest1 = o; o = al(o + N * 4);
+    p.o_bid2 = o; o = al(o + N * 1);
+    p.o_K2 = o; o = al(o + N * 8);
+    p.o_dest2 = o; o = al(o + N * 4);
+    p.o_U2 = o; o = al(o + N * 4);
+    p.o_tmpU = o; o = al(o + N * 8);
+    p.o_leafst = o; o = al(o + (p.NL + 1) * 8);
+    p.o_ucnt = o; o = al(o + p.NL * 8);
+    p.o_ubase = o; o = al(o + (p.NL + 1) * 8);
+    p.o_pay = o; o = al(o + N * 8);
+    p.o_kbase = o; o = al(o + ((size_t)p.B1 + 1) * 8);
+    p.bytes = o;
+    return p;
+}
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ void stage(uint64_t *dst, const uint64_t *__restrict__ src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// sort key of one W-word key: combinatorial rank (mode 1) or raw word (mode 0);
+// *ones receives the number of set bits among the low n_bits.
+template <int W>
+__device__ __forceinline__ uint64_t sort_key(const uint64_t *__restrict__ k, int mode, int n_bits,
+                                             int kcols, const uint64_t *bt, int *ones) {
+    uint64_t r = 0;
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        uint64_t x = __ldg(k + w);
+        const int hi = n_bits - 64 * w;
+        if (hi < 64) x &= hi <= 0 ? 0ull : ((1ull << hi) - 1);
+        if (mode == 0) {
+            if (w == 0) r = x;
+            c += __popcll(x);
+            continue;
+        }
+        for (; x; x &= x - 1) {
+            const int pos = 64 * w + __ffsll((long long)x) - 1;
+            c++;
+            if (c < kcols) r += bt[pos * kcols + c];
+        }
+    }
+    *ones = c;
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ void unrank_to(uint64_t r, int mode, int n_bits, int n_ones, int kcols,
+                                          const uint64_t *bt, uint64_t *__restrict__ out) {
+    uint64_t x[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) x[w] = 0;
+    if (mode == 0) {
+        x[0] = r;
+    } else {
+        int c = n_bits - 1;
+        for (int t = n_ones; t >= 1; t--) {
+            while (c >= t && bt[c * kcols + t] > r) c--;
+            if (c >= t) r -= bt[c * kcols + t];
+            if (c >= 0) x[(c >> 6) & (W - 1)] |= 1ull << (c & 63);
+            c--;
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < W; w++) out[w] = x[w];
+}
+
+// number of entries of the sorted array S[0 .. 2^lg) that are < x (S[last] >= x)
+__device__ __forceinline__ int count_less(const uint64_t *S, int lg, uint64_t x) {
+    int b = 0;
+    for (int step = (1 << lg) >> 1; step >= 1; step >>= 1)
+        if (S[b + step - 1] < x) b += step;
+    return b;
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void build_bt(uint64_t *bt, int n_bits, int kcols) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int m = 0; m < n_bits; m++)
+        for (int k = 0; k < kcols; k++) {
+            uint64_t v;
+            if (k == 0) v = 1;
+            else if (m == 0) v = 0;
+            else {
+                const uint64_t a = bt[(m - 1) * kcols + k - 1], b = bt[(m - 1) * kcols + k];
+                v = (a + b < a) ? ~0ull : a + b;
+            }
+            bt[m * kcols + k] = v;
+        }
+}
+
+template <int W>
+__global__ void __launch_bounds__(T)
+    sample_keys(const uint64_t *__restrict__ keys, int64_t N, int64_t NS, int mode, int n_bits,
+                int kcols, const uint64_t *__restrict__ bt_g, uint64_t *__restrict__ samp,
+                uint32_t *__restrict__ sidx) {
+    __shared__ uint64_t bt[BT_MAX];
+    stage(bt, bt_g, n_bits * kcols);
+    __syncthreads();
+    for (int64_t j = blockIdx.x * (int64_t)T + threadIdx.x; j < NS; j += (int64_t)gridDim.x * T) {
+        const int64_t pos = (int64_t)(((unsigned __int128)j * (unsigned __int128)N) / NS);
+        int ones;
+        samp[j] = sort_key<W>(keys + pos * W, mode, n_bits, kcols, bt, &ones);
+        sidx[j] = (uint32_t)j;
+    }
+}
+
+__global__ void make_splitters(const uint64_t *__restrict__ sorted, int64_t NS, int64_t NL,
+                               uint64_t *__restrict__ LS) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < NL;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (j == NL - 1) {
+            LS[j] = ~0ull;
+        } else {
+            int64_t s = (j + 1) * (NS / NL) - 1;
+            if (NS / NL == 0) s = (int64_t)(((double)(j + 1) / NL) * NS) - 1;
+            if (s < 0) s = 0;
+            if (s >= NS) s = NS - 1;
+            LS[j] = sorted[s];
+        }
+    }
+}
+
+constexpr int U1 = 4;   // keys per thread in flight in the partition passes
+constexpr int UG = 8;   // gathers in flight per thread in the reverse-index passes
+
+template <int W>
+__global__ void __launch_bounds__(T)
+    hist1(const uint64_t *__restrict__ keys, int64_t N, int64_t per_cta, int mode, int n_bits,
+          int n_ones, int kcols, const uint64_t *__restrict__ bt_g,
+          const uint64_t *__restrict__ LS, int B1, int log2B1, uint16_t *__restrict__ bid1,
+          uint32_t *__restrict__ H1, int32_t *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint64_t *S1 = (uint64_t *)sm;
+    uint64_t *bt = S1 + B1;
+    uint32_t *h = (uint32_t *)(bt + BT_MAX);
+    for (int b = threadIdx.x; b < B1; b += T) {
+        S1[b] = LS[(int64_t)b * B2 + B2 - 1];
+        h[b] = 0;
+    }
+    if (mode == 1) stage(bt, bt_g, n_bits * kcols);
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * per_cta;
+    int64_t end = beg + per_cta;
+    if (end > N) end = N;
+    bool bad = false;
+    for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += (int64_t)T * U1) {
+        uint64_t x[U1];
+        int ones[U1];
+#pragma unroll
+        for (int u = 0; u < U1; u++) {
+            const int64_t i = i0 + (int64_t)u * T;
+            x[u] = 0;
+            ones[u] = n_ones;
+            if (i < end) x[u] = sort_key<W>(keys + i * W, mode, n_bits, kcols, bt, &ones[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U1; u++) {
+            const int64_t i = i0 + (int64_t)u * T;
+            if (i < end) {
+                if (n_ones >= 0 && ones[u] != n_ones) bad = true;
+                const int b = count_less(S1, log2B1, x[u]);
+                bid1[i] = (uint16_t)b;
+                atomicAdd(&h[b], 1u);
+            }
+        }
+    }
+    if (bad && status) *status = CUSCI_ERR_INVALID;
+    __syncthreads();
+    for (int b = threadIdx.x; b < B1; b += T) H1[(int64_t)blockIdx.x * B1 + b] = h[b];
+}
+
+// bucket totals over all blocks (level-1 order of the leaf array)
+__global__ void bucket_totals(const uint32_t *__restrict__ H1, int G, int B1,
+                              int64_t *__restrict__ tot) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B1; b += gridDim.x * blockDim.x) {
+        int64_t s = 0;
+        for (int c = 0; c < G; c++) s += H1[(int64_t)c * B1 + b];
+        tot[b] = s;
+    }
+}
+
+__global__ void widen_u32(const uint32_t *__restrict__ h, int64_t n, int64_t *__restrict__ o) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        o[k] = h[k];
+}
+
+// warp-aggregated slot reservation: lanes with the same bucket b get
+// consecutive slots from the shared counter run[b]
+__device__ __forceinline__ uint64_t reserve_slot(unsigned long long *run, uint32_t b, bool valid,
+                                                 int lane) {
+    const unsigned peers = __match_any_sync(FULL, b);
+    const int leader = __ffs(peers) - 1;
+    const int below = __popc(peers & ((1u << lane) - 1u));
+    unsigned long long base = 0;
+    if (valid && lane == leader) base = atomicAdd(&run[b], (unsigned long long)__popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    return base + below;
+}
+
+template <int W>
+__global__ void __launch_bounds__(T)
+    scatter1(const uint64_t *__restrict__ keys, int64_t N, int64_t per_cta, int mode, int n_bits,
+             int kcols, const uint64_t *__restrict__ bt_g, const uint16_t *__restrict__ bid1,
+             int B1, const int64_t *__restrict__ base1, uint64_t *__restrict__ K1,
+             uint32_t *__restrict__ dest1) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned long long *run = (unsigned long long *)sm;
+    uint64_t *bt = (uint64_t *)(run + B1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b = threadIdx.x; b < B1; b += T)
+        run[b] = (unsigned long long)base1[(int64_t)blockIdx.x * B1 + b];
+    if (mode == 1) stage(bt, bt_g, n_bits * kcols);
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * per_cta;
+    int64_t end = beg + per_cta;
+    if (end > N) end = N;
+    for (int64_t i0 = beg + wid * 32; i0 < end; i0 += (int64_t)WARPS * 32 * U1) {
+        uint64_t x[U1];
+        uint32_t b[U1];
+#pragma unroll
+        for (int u = 0; u < U1; u++) {
+            const int64_t i = i0 + (int64_t)u * WARPS * 32 + lane;
+            b[u] = (uint32_t)B1;
+            x[u] = 0;
+            if (i < end) {
+                int ones;
+                b[u] = bid1[i];
+                x[u] = sort_key<W>(keys + i * W, mode, n_bits, kcols, bt, &ones);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U1; u++) {
+            const int64_t i = i0 + (int64_t)u * WARPS * 32 + lane;
+            const bool valid = i < end;
+            const uint64_t d = reserve_slot(run, b[u], valid, lane);
+            if (valid) {
+                K1[d] = x[u];
+                dest1[i] = (uint32_t)d;
+            }
+        }
+    }
+}
+
+// one block per level-1 bucket: B2-way split into leaf buckets.  The bucket's
+// entries sit in G segments (one per level-1 block, CTA-major layout); its
+// leaves are written contiguously from kbase[b1].
+__global__ void __launch_bounds__(T)
+    level2(const uint64_t *__restrict__ K1, int64_t N, const int64_t *__restrict__ base1,
+           const uint32_t *__restrict__ H1, int G, int B1, const int64_t *__restrict__ kbase,
+           const uint64_t *__restrict__ LS, int64_t NL, uint8_t *__restrict__ bid2,
+           uint64_t *__restrict__ K2, uint32_t *__restrict__ dest2,
+           int64_t *__restrict__ leaf_start) {
+    __shared__ uint64_t L[B2];
+    __shared__ uint32_t h[B2];
+    __shared__ unsigned long long run[B2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int b1 = blockIdx.x;
+    const int64_t kb = kbase[b1];
+    for (int t = threadIdx.x; t < B2; t += T) {
+        L[t] = LS[(int64_t)b1 * B2 + t];
+        h[t] = 0;
+    }
+    __syncthreads();
+    for (int c = wid; c < G; c += WARPS) {
+        const int64_t sb = base1[(int64_t)c * B1 + b1];
+        const int64_t len = H1[(int64_t)c * B1 + b1];
+        for (int64_t k0 = 0; k0 < len; k0 += 32 * U1) {
+            uint64_t x[U1];
+#pragma unroll
+            for (int u = 0; u < U1; u++) {
+                const int64_t k = k0 + u * 32 + lane;
+                x[u] = k < len ? K1[sb + k] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U1; u++) {
+                const int64_t k = k0 + u * 32 + lane;
+                if (k < len) {
+                    const int b = count_less(L, LOG2_B2, x[u]);
+                    bid2[sb + k] = (uint8_t)b;
+                    atomicAdd(&h[b], 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (wid == 0) {
+        constexpr int PER = B2 / 32;
+        uint32_t cnt[PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; q++) { cnt[q] = h[lane * PER + q]; sum += cnt[q]; }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t ex = inc - sum;
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int t = lane * PER + q;
+            run[t] = (unsigned long long)(kb + ex);
+            leaf_start[(int64_t)b1 * B2 + t] = kb + ex;
+            ex += cnt[q];
+        }
+    }
+    if (b1 == (int)gridDim.x - 1 && threadIdx.x == 0) leaf_start[NL] = N;
+    __syncthreads();
+    for (int c = wid; c < G; c += WARPS) {
+        const int64_t sb = base1[(int64_t)c * B1 + b1];
+        const int64_t len = H1[(int64_t)c * B1 + b1];
+        for (int64_t k0 = 0; k0 < len; k0 += 32 * U1) {
+            uint64_t x[U1];
+            uint32_t bb[U1];
+#pragma unroll
+            for (int u = 0; u < U1; u++) {
+                const int64_t k = k0 + u * 32 + lane;
+                bb[u] = (uint32_t)B2;
+                x[u] = 0;
+                if (k < len) {
+                    bb[u] = bid2[sb + k];
+                    x[u] = K1[sb + k];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U1; u++) {
+                const int64_t k = k0 + u * 32 + lane;
+                const bool valid = k < len;
+                const uint64_t d = reserve_slot(run, bb[u], valid, lane);
+                if (valid) {
+                    K2[d] = x[u];
+                    dest2[sb + k] = (uint32_t)d;
+                }
+            }
+        }
+    }
+}
+
+struct LeafSmem {
+    uint64_t A[LEAF_CAP];
+    uint64_t B[LEAF_CAP];
+    uint32_t hist[256];
+    uint32_t run[256];
+    uint32_t ttot[256];
+    uint16_t wcnt[WARPS][256];
+    uint64_t red_lo[WARPS], red_hi[WARPS];
+    uint32_t red_cnt[WARPS];
+};
+
+// one pass of a stable LSD radix sort of a[0..n) into b[0..n) on the 8-bit
+// digit at `shift`; pa / pb: optional 32-bit payload moved along (a, b, pa, pb
+// in shared or global memory)
+template <bool PAYLOAD>
+__device__ void leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, uint32_t *pb,
+                          int64_t n, int shift, LeafSmem &S) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < 256; d += T) S.hist[d] = 0;
+    __syncthreads();
+    for (int64_t k = threadIdx.x; k < n; k += T) atomicAdd(&S.hist[(a[k] >> shift) & 255], 1u);
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t c[8], s = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) { c[q] = S.hist[lane * 8 + q]; s += c[q]; }
+        uint32_t inc = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t ex = inc - s;
+#pragma unroll
+        for (int q = 0; q < 8; q++) { S.run[lane * 8 + q] = ex; ex += c[q]; }
+    }
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < n; t0 += LTILE) {
+        for (int q = threadIdx.x; q < WARPS * 256; q += T) (&S.wcnt[0][0])[q] = 0;
+        __syncthreads();
+        uint64_t v[LRI];
+        uint32_t dg[LRI], rk[LRI];
+#pragma unroll
+        for (int r = 0; r < LRI; r++) {
+            const int64_t k = t0 + wid * (LRI * 32) + r * 32 + lane;
+            v[r] = k < n ? a[k] : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < LRI; r++) {
+            const int64_t k = t0 + wid * (LRI * 32) + r * 32 + lane;
+            const bool valid = k < n;
+            dg[r] = valid ? (uint32_t)((v[r] >> shift) & 255) : 256u;
+            const unsigned peers = __match_any_sync(FULL, dg[r]);
+            const int below = __popc(peers & ((1u << lane) - 1u));
+            uint32_t prev = valid ? S.wcnt[wid][dg[r]] : 0;
+            rk[r] = prev + below;
+            __syncwarp();
+            if (valid && below == 0) S.wcnt[wid][dg[r]] = (uint16_t)(prev + __popc(peers));
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += T) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < WARPS; w++) {
+                const uint32_t c = S.wcnt[w][d];
+                S.wcnt[w][d] = (uint16_t)s;
+                s += c;
+            }
+            S.ttot[d] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < LRI; r++) {
+            if (dg[r] < 256) {
+                const uint32_t dst = S.run[dg[r]] + S.wcnt[wid][dg[r]] + rk[r];
+                b[dst] = v[r];
+                if (PAYLOAD) pb[dst] = pa[t0 + wid * (LRI * 32) + r * 32 + lane];
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += T) S.run[d] += S.ttot[d];
+        __syncthreads();
+    }
+}
+
+// walks the sorted keys a[0..n) (positions in the low pbits, or in pos[] when
+// given) and writes the local unique id of every position and the distinct keys
+__device__ void leaf_walk(const uint64_t *a, const uint32_t *pos, int64_t n, int pbits,
+                          uint64_t r_lo, int64_t ls, uint32_t *__restrict__ U2,
+                          uint64_t *__restrict__ tmpU, int64_t *__restrict__ ucnt_out,
+                          LeafSmem &S) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t chunk = ((n + WARPS - 1) / WARPS + 31) / 32 * 32;
+    const int64_t wb = wid * chunk;
+    const int64_t we = wb + chunk < n ? wb + chunk : n;
+    const uint64_t pmask = pbits == 0 ? 0ull : (~0ull >> (64 - pbits));
+    uint32_t cnt = 0;
+    for (int64_t k = wb + lane; k < we + 31 && k - lane < we; k += 32) {
+        bool head = false;
+        if (k < we) head = (k == 0) || ((a[k - 1] >> pbits) != (a[k] >> pbits));
+        cnt += __popc(__ballot_sync(FULL, head));
+    }
+    if (lane == 0) S.red_cnt[wid] = cnt;
+    __syncthreads();
+    uint32_t base = 0, total = 0;
+    for (int w = 0; w < WARPS; w++) {
+        const uint32_t c = S.red_cnt[w];
+        if (w < wid) base += c;
+        total += c;
+    }
+    for (int64_t k = wb + lane; k - lane < we; k += 32) {
+        bool head = false;
+        uint64_t v = 0;
+        if (k < we) {
+            v = a[k];
+            head = (k == 0) || ((a[k - 1] >> pbits) != (v >> pbits));
+        }
+        const unsigned bal = __ballot_sync(FULL, head);
+        if (k < we) {
+            const uint32_t uid = base + __popc(bal & ((2u << lane) - 1u)) - 1u;
+            const int64_t p = pos ? (int64_t)pos[k] : (int64_t)(v & pmask);
+            U2[ls + p] = uid;
+            if (head) tmpU[ls + uid] = (v >> pbits) + r_lo;
+        }
+        base += __popc(bal);
+    }
+    if (threadIdx.x == 0) *ucnt_out = total;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(T, 3)
+    leaf_sort(uint64_t *__restrict__ K2, uint64_t *__restrict__ scratch,
+              uint32_t *__restrict__ pay, int64_t N, int64_t NL,
+              const int64_t *__restrict__ leaf_start, uint32_t *__restrict__ U2,
+              uint64_t *__restrict__ tmpU, int64_t *__restrict__ ucnt) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    LeafSmem &S = *reinterpret_cast<LeafSmem *>(sm);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t leaf = blockIdx.x; leaf < NL; leaf += gridDim.x) {
+        const int64_t ls = leaf_start[leaf];
+        const int64_t n = leaf_start[leaf + 1] - ls;
+        if (n <= 0) {
+            if (threadIdx.x == 0) ucnt[leaf] = 0;
+            continue;
+        }
+        uint64_t lo = ~0ull, hi = 0;
+        for (int64_t k = threadIdx.x; k < n; k += T) {
+            const uint64_t x = K2[ls + k];
+            lo = x < lo ? x : lo;
+            hi = x > hi ? x : hi;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t y = __shfl_xor_sync(FULL, lo, o), z = __shfl_xor_sync(FULL, hi, o);
+            lo = y < lo ? y : lo;
+            hi = z > hi ? z : hi;
+        }
+        if (lane == 0) { S.red_lo[wid] = lo; S.red_hi[wid] = hi; }
+        __syncthreads();
+        uint64_t r_lo = S.red_lo[0], r_hi = S.red_hi[0];
+        for (int w = 1; w < WARPS; w++) {
+            r_lo = S.red_lo[w] < r_lo ? S.red_lo[w] : r_lo;
+            r_hi = S.red_hi[w] > r_hi ? S.red_hi[w] : r_hi;
+        }
+        const int rb = r_hi == r_lo ? 0 : 64 - __clzll((long long)(r_hi - r_lo));
+        const int pbits = n <= 1 ? 0 : 64 - __clzll((long long)(n - 1));
+        if (n <= LEAF_CAP && rb + pbits <= 64) {
+            // packed (key - min) << pbits | position, sorted in shared memory
+            uint64_t *a = S.A, *b = S.B;
+            for (int64_t k = threadIdx.x; k < n; k += T)
+                a[k] = ((K2[ls + k] - r_lo) << pbits) | (uint64_t)k;
+            __syncthreads();
+            for (int shift = pbits; shift < pbits + rb; shift += 8) {
+                leaf_pass<false>(a, b, nullptr, nullptr, n, shift, S);
+                uint64_t *t = a; a = b; b = t;
+            }
+            leaf_walk(a, nullptr, n, pbits, r_lo, ls, U2, tmpU, ucnt + leaf, S);
+        } else {
+            // global memory: keys (key - min) with positions in a separate array
+            uint64_t *a = K2 + ls, *b = scratch + ls;
+            uint32_t *pa = pay + ls, *pb = pay + N + ls;
+            for (int64_t k = threadIdx.x; k < n; k += T) {
+                a[k] = K2[ls + k] - r_lo;
+                pa[k] = (uint32_t)k;
+            }
+            __syncthreads();
+            for (int shift = 0; shift < rb; shift += 8) {
+                leaf_pass<true>(a, b, pa, pb, n, shift, S);
+                uint64_t *t = a; a = b; b = t;
+                uint32_t *tp = pa; pa = pb; pb = tp;
+            }
+            leaf_walk(a, pa, n, 0, r_lo, ls, U2, tmpU, ucnt + leaf, S);
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(T)
+    compact_unique(const uint64_t *__restrict__ tmpU, const int64_t *__restrict__ leaf_start,
+                   const int64_t *__restrict__ ucnt, const int64_t *__restrict__ ubase,
+                   int64_t NL, int mode, int n_bits, int n_ones, int kcols,
+                   const uint64_t *__restrict__ bt_g, uint64_t *__restrict__ unique,
+                   int64_t *__restrict__ n_unique) {
+    __shared__ uint64_t bt[BT_MAX];
+    if (mode == 1) stage(bt, bt_g, n_bits * kcols);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)T + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * T) >> 5;
+    for (int64_t leaf = warp; leaf < NL; leaf += nw) {
+        const int64_t ls = leaf_start[leaf], c = ucnt[leaf], ub = ubase[leaf];
+        for (int64_t k = lane; k < c; k += 32) {
+            if (mode == 0) unique[ub + k] = tmpU[ls + k];
+            else unrank_to<W>(tmpU[ls + k], mode, n_bits, n_ones, kcols, bt, unique + (ub + k) * W);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_unique = ubase[NL];
+}
+
+__global__ void __launch_bounds__(T)
+    unscatter2(const int64_t *__restrict__ base1, const uint32_t *__restrict__ H1, int G, int B1,
+               const uint8_t *__restrict__ bid2, uint32_t *__restrict__ dest2_u1,
+               const uint32_t *__restrict__ U2, const int64_t *__restrict__ ubase) {
+    const int b1 = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = wid; c < G; c += WARPS) {
+        const int64_t sb = base1[(int64_t)c * B1 + b1];
+        const int64_t len = H1[(int64_t)c * B1 + b1];
+        for (int64_t k0 = 0; k0 < len; k0 += 32 * UG) {
+            uint32_t d[UG], lf[UG], u[UG];
+#pragma unroll
+            for (int q = 0; q < UG; q++) {
+                const int64_t k = k0 + q * 32 + lane;
+                d[q] = k < len ? dest2_u1[sb + k] : 0u;
+                lf[q] = k < len ? bid2[sb + k] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < UG; q++) {
+                const int64_t k = k0 + q * 32 + lane;
+                u[q] = k < len ? U2[d[q]] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < UG; q++) {
+                const int64_t k = k0 + q * 32 + lane;
+                if (k < len)
+                    dest2_u1[sb + k] = (uint32_t)(u[q] + ubase[(int64_t)b1 * B2 + lf[q]]);
+            }
+        }
+    }
+}
+
+template <typename IDX>
+__global__ void __launch_bounds__(256)
+    unscatter1(const uint32_t *__restrict__ dest1, const uint32_t *__restrict__ U1v, int64_t N,
+               IDX *__restrict__ inverse) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < N; i0 += stride * UG) {
+        uint32_t d[UG], u[UG];
+#pragma unroll
+        for (int q = 0; q < UG; q++) {
+            const int64_t i = i0 + q * stride;
+            d[q] = i < N ? dest1[i] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < UG; q++) {
+            const int64_t i = i0 + q * stride;
+            u[q] = i < N ? U1v[d[q]] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < UG; q++) {
+            const int64_t i = i0 + q * stride;
+            if (i < N) inverse[i] = (IDX)u[q];
+        }
+    }
+}
+
+cusci_status set_smem(const void *fn, size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e == cudaSuccess ? CUSCI_OK : cuda_fail(e, "dedup: shared-memory attribute");
+}
+
+template <int W>
+cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_t *unique,
+                 void *inverse, int index_bytes, int64_t *d_n_unique, int32_t *status,
+                 cudaStream_t st) {
+    using namespace radix;
+    uint64_t *bt = (uint64_t *)(ws + p.o_bt);
+    Key<1> *samp = (Key<1> *)(ws + p.o_samp), *samp2 = (Key<1> *)(ws + p.o_samp2);
+    uint32_t *sidx = (uint32_t *)(ws + p.o_sidx), *sidx2 = (uint32_t *)(ws + p.o_sidx2);
+    uint32_t *shist = (uint32_t *)(ws + p.o_shist);
+    int64_t *sbase = (int64_t *)(ws + p.o_sbase);
+    int64_t *scanws = (int64_t *)(ws + p.o_scanws);
+    uint64_t *LS = (uint64_t *)(ws + p.o_LS);
+    uint32_t *H1 = (uint32_t *)(ws + p.o_H1);
+    int64_t *base1 = (int64_t *)(ws + p.o_base1);
+    uint16_t *bid1 = (uint16_t *)(ws + p.o_bid1);
+    uint64_t *K1 = (uint64_t *)(ws + p.o_K1);
+    uint32_t *dest1 = (uint32_t *)(ws + p.o_dest1);
+    uint8_t *bid2 = (uint8_t *)(ws + p.o_bid2);
+    uint64_t *K2 = (uint64_t *)(ws + p.o_K2);
+    uint32_t *dest2 = (uint32_t *)(ws + p.o_dest2);
+    uint32_t *U2 = (uint32_t *)(ws + p.o_U2);
+    uint64_t *tmpU = (uint64_t *)(ws + p.o_tmpU);
+    int64_t *leafst = (int64_t *)(ws + p.o_leafst);
+    int64_t *ucnt = (int64_t *)(ws + p.o_ucnt);
+    int64_t *ubase = (int64_t *)(ws + p.o_ubase);
+    const int sms = sm_count();
+    int launches = 0;
+
+    build_bt<<<1, 32, 0, st>>>(bt, p.n_bits, p.kcols);
+    launches++;
+    sample_keys<W><<<sms * 4, T, 0, st>>>(keys, p.N, p.NS, p.mode, p.n_bits, p.kcols, bt, (uint64_t *)samp,
+                                          sidx);
+    launches++;
+    // sort the sample with the LSD building blocks
+    {
+        static bool attr = false;
+        const size_t smem = sizeof(DownSmem<1>);
+        if (!attr) {
+            cusci_status rc = set_smem((const void *)downsweep<1>, smem);
+            if (rc != CUSCI_OK) return rc;
+            attr = true;
+        }
+        const int64_t nh = (int64_t)RADIX * p.gs;
+        for (int pass = 0; pass < p.s_passes; pass++) {
+            upsweep<1><<<p.gs, RT, 0, st>>>(samp, p.NS, pass * RBITS, p.gs_per, shist);
+            widen_u32<<<64, 256, 0, st>>>(shist, nh, sbase);
+            cusci_status rc = exclusive_scan_i64(sbase, nh, sbase, scanws, st);
+            if (rc != CUSCI_OK) return rc;
+            downsweep<1><<<p.gs, RT, smem, st>>>(samp, sidx, samp2, sidx2, p.NS, pass * RBITS,
+                                                 p.gs_per, sbase);
+            launches += 3;
+            Key<1> *tk = samp; samp = samp2; samp2 = tk;
+            uint32_t *ti = sidx; sidx = sidx2; sidx2 = ti;
+        }
+    }
+    make_splitters<<<(int)((p.NL + 255) / 256), 256, 0, st>>>((const uint64_t *)samp, p.NS, p.NL,
+                                                               LS);
+    launches++;
+    // level 1
+    const size_t sm_h1 = (size_t)p.B1 * 8 + BT_MAX * 8 + (size_t)p.B1 * 4;
+    const size_t sm_x1 = (size_t)p.B1 * 8 + BT_MAX * 8;
+    {
+        static bool attr = false;
+        if (!attr) {
+            cusci_status rc = set_smem((const void *)hist1<W>, (size_t)MAX_B1 * 12 + BT_MAX * 8);
+            if (rc == CUSCI_OK) rc = set_smem((const void *)scatter1<W>, (size_t)MAX_B1 * 8 + BT_MAX * 8);
+            if (rc == CUSCI_OK) rc = set_smem((const void *)leaf_sort, sizeof(LeafSmem));
+            if (rc != CUSCI_OK) return rc;
+            attr = true;
+        }
+    }
+    hist1<W><<<p.G, T, sm_h1, st>>>(keys, p.N, p.per_cta, p.mode, p.n_bits, p.n_ones, p.kcols, bt,
+                                    LS, p.B1, p.log2B1, bid1, H1, status);
+    const int64_t nh1 = (int64_t)p.B1 * p.G;
+    widen_u32<<<sms * 2, 256, 0, st>>>(H1, nh1, base1);
+    cusci_status rc = exclusive_scan_i64(base1, nh1, base1, scanws, st);
+    if (rc != CUSCI_OK) return rc;
+    scatter1<W><<<p.G, T, sm_x1, st>>>(keys, p.N, p.per_cta, p.mode, p.n_bits, p.kcols, bt, bid1,
+                                       p.B1, base1, K1, dest1);
+    int64_t *kbase = (int64_t *)(ws + p.o_kbase);
+    bucket_totals<<<(p.B1 + 255) / 256, 256, 0, st>>>(H1, p.G, p.B1, kbase);
+    rc = exclusive_scan_i64(kbase, p.B1, kbase, scanws, st);
+    if (rc != CUSCI_OK) return rc;
+    launches += 4;
+    // level 2
+    level2<<<p.B1, T, 0, st>>>(K1, p.N, base1, H1, p.G, p.B1, kbase, LS, p.NL, bid2, K2, dest2,
+                               leafst);
+    launches++;
+    // leaves
+    uint32_t *pay = (uint32_t *)(ws + p.o_pay);
+    leaf_sort<<<sms * 3, T, sizeof(LeafSmem), st>>>(K2, K1, pay, p.N, p.NL, leafst, U2, tmpU, ucnt);
+    launches++;
+    rc = exclusive_scan_i64(ucnt, p.NL, ubase, scanws, st);
+    if (rc != CUSCI_OK) return rc;
+    compact_unique<W><<<sms * 4, T, 0, st>>>(tmpU, leafst, ucnt, ubase, p.NL, p.mode, p.n_bits,
+                                             p.n_ones, p.kcols, bt, unique, d_n_unique);
+    unscatter2<<<p.B1, T, 0, st>>>(base1, H1, p.G, p.B1, bid2, dest2, U2, ubase);
+    if (index_bytes == 4)
+        unscatter1<int32_t><<<sms * 4, 256, 0, st>>>(dest1, dest2, p.N, (int32_t *)inverse);
+    else
+        unscatter1<int64_t><<<sms * 4, 256, 0, st>>>(dest1, dest2, p.N, (int64_t *)inverse);
+    launches += 3;
+    CUSCI_LAUNCHED(launches, "sample-sort dedup");
+    return CUSCI_OK;
+}
+
+}  // namespace ss
+
+bool ss_eligible(int64_t N, int W, int n_bits, int n_ones) {
+    int mode, kb;
+    return ss::eligible(N, W, n_bits, n_ones, &mode, &kb);
+}
+
+size_t ss_workspace(int64_t N, int W, int n_bits, int n_ones) {
+    int mode, kb;
+    if (!ss::eligible(N, W, n_bits, n_ones, &mode, &kb)) return 0;
+    return ss::make_plan(N, W, n_bits, n_ones, mode, kb).bytes;
+}
+
+cusci_status ss_dedup(const uint64_t *keys, int64_t N, int W, int n_bits, int n_ones, void *ws,
+                      size_t ws_bytes, uint64_t *unique, void *inverse, int index_bytes,
+                      int64_t *d_n_unique, int32_t *status, cudaStream_t st) {
+    int mode, kb;
+    if (!ss::eligible(N, W, n_bits, n_ones, &mode, &kb))
+        return fail(CUSCI_ERR_INVALID, "dedup: sample-sort path not applicable");
+    const ss::Plan p = ss::make_plan(N, W, n_bits, n_ones, mode, kb);
+    if (ws_bytes < p.bytes)
+        return fail(CUSCI_ERR_OOM, "cusci_dedup: workspace %zu < %zu bytes", ws_bytes, p.bytes);
+    if (W == 1)
+        return ss::run<1>(p, keys, (unsigned char *)ws, unique, inverse, index_bytes, d_n_unique,
+                          status, st);
+    return ss::run<2>(p, keys, (unsigned char *)ws, unique, inverse, index_bytes, d_n_unique,
+                      status, st);
+}
+
+}  // namespace cusci

@@ -103,18 +103,27 @@ struct HpsiEmit {
     }
 };
 
-template <int W>
+template <int W, bool STAGE>
 __global__ void __launch_bounds__(32 * EW)
     hpsi_kernel(SysView v, Table tb, const uint64_t *__restrict__ S, int64_t nS, double eps,
-                const double *__restrict__ psi, double *__restrict__ hpsi) {
+                const double *__restrict__ psi, double *__restrict__ hpsi,
+                int32_t *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
+    WarpStage st;
+    WarpStage *stp = nullptr;
+    if (STAGE) {
+        stage_init(st, smem + (threadIdx.x >> 5) * stage_bytes(v.slab, v.mrow), v.slab, v.mrow,
+                   lane, status);
+        stp = &st;
+    }
     const int64_t warp = (int64_t)blockIdx.x * EW + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * EW;
     for (int64_t i = warp; i < nS; i += nwarps) {
         Src<W> s;
         decode<W>(S + i * W, v.norb, s);
         HpsiEmit<W> em{&tb, psi, 0.0};
-        visit_source<W>(v, s, eps, lane, em);
+        visit_source<W>(v, s, eps, lane, em, stp);
         double a = em.acc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a = __dadd_rn(a, __shfl_xor_sync(FULL, a, o));
@@ -218,12 +227,30 @@ cusci_status compute_hpsi(const cusci_system *sys, const uint64_t *d_S, int64_t 
     if (ib > sm_count() * 8) ib = sm_count() * 8;
     int64_t want = (nS + EW - 1) / EW;
     int grid = (int)(want < sm_count() * 8 ? want : sm_count() * 8);
-    if (sys->W == 1) {
+    const size_t smem = (size_t)EW * stage_bytes(v.slab, v.mrow);
+    if (sys->W == 1 && smem <= 200 * 1024) {
         insert_S<1><<<ib, 256, 0, st>>>(tb, d_S, nS, d_status);
-        hpsi_kernel<1><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp);
+        static size_t attr = 0;
+        if (attr < smem) {
+            cudaError_t e2 = cudaFuncSetAttribute(hpsi_kernel<1, true>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "energy: shared-memory attribute");
+            attr = smem;
+        }
+        int per_sm = 0;
+        cudaError_t e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hpsi_kernel<1, true>,
+                                                                       32 * EW, smem);
+        if (e3 != cudaSuccess || per_sm < 1) per_sm = 1;
+        int g1 = (int)(want < sm_count() * per_sm ? want : sm_count() * per_sm);
+        if (g1 < 1) g1 = 1;
+        hpsi_kernel<1, true><<<g1, 32 * EW, smem, st>>>(v, tb, d_S, nS, eps, d_psi, hp, d_status);
+    } else if (sys->W == 1) {
+        insert_S<1><<<ib, 256, 0, st>>>(tb, d_S, nS, d_status);
+        hpsi_kernel<1, false><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp, d_status);
     } else {
         insert_S<2><<<ib, 256, 0, st>>>(tb, d_S, nS, d_status);
-        hpsi_kernel<2><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp);
+        hpsi_kernel<2, false><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp, d_status);
     }
     CUSCI_LAUNCHED(2, "energy: H psi");
     return CUSCI_OK;

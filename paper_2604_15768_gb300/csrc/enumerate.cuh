@@ -73,8 +73,12 @@ __device__ __forceinline__ void decode(const uint64_t *__restrict__ det, int nor
     }
 }
 
-__device__ __forceinline__ uint32_t par_bit(const uint64_t par[2], int so) {
-    return (uint32_t)((par[so & 1] >> (so >> 1)) & 1ull);
+// two-entry selects keep per-spin arrays in registers (no dynamic indexing)
+__device__ __forceinline__ uint64_t sel2(const uint64_t (&x)[2], int k) { return k ? x[1] : x[0]; }
+__device__ __forceinline__ uint32_t sel2(const uint32_t (&x)[2], int k) { return k ? x[1] : x[0]; }
+
+__device__ __forceinline__ uint32_t par_bit(const uint64_t (&par)[2], int so) {
+    return (uint32_t)((sel2(par, so & 1) >> (so >> 1)) & 1ull);
 }
 
 template <int W>
@@ -157,7 +161,7 @@ __device__ int64_t count_source(const SysView &v, const Src<W> &s, double eps, i
             for (int c = 0; c < nchunk; c++) {
                 const int pa = lane + 32 * c;
                 bool keep = false;
-                if (pa < n && ((s.vir[sg] >> pa) & 1ull)) {
+                if (pa < n && ((sel2(s.vir, sg) >> pa) & 1ull)) {
                     double acc = single_value<W>(v, s, i, pa);
                     keep = fabs(acc) > eps;
                 }
@@ -180,11 +184,11 @@ __device__ int64_t count_source(const SysView &v, const Src<W> &s, double eps, i
                     const int pj = j >> 1, sj = j & 1;
                     const int kind = (si == sj) ? 0 : 1;
                     const uint64_t *__restrict__ mrow =
-                        v.mask + ((size_t)(kind * n + pi) * n + pj) * n;
+                        v.mask + ((size_t)(kind * n + pi) * n + pj) * v.mrow;
                     for (int c = 0; c < nchunk; c++) {
                         const int pa = lane + 32 * c;
-                        if (pa < n && ((s.vir[si] >> pa) & 1ull))
-                            doubles += __popcll(__ldg(mrow + pa) & s.vir[sj]);
+                        if (pa < n && ((sel2(s.vir, si) >> pa) & 1ull))
+                            doubles += __popcll(__ldg(mrow + pa) & sel2(s.vir, sj));
                     }
                 }
             }
@@ -197,6 +201,109 @@ __device__ int64_t count_source(const SysView &v, const Src<W> &s, double eps, i
 }
 
 
+// ---------------------------------------------------------------- staging
+// Per-warp double buffer in shared memory holding, for one occupied pair
+// (i, j), its integral slab T[pair][a][b] and its screening-mask row, filled by
+// bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) one
+// pair ahead of the pair being written out.
+struct WarpStage {
+    double *slab0;     // buffer b at slab0 + b * slab
+    uint64_t *mrow0;   // buffer b at mrow0 + b * mrow
+    int slab, mrow;
+    uint64_t *bar;    // two mbarriers
+    uint32_t phase;   // bit b: parity expected next on barrier b
+    int next;         // buffer that receives the next first-pair copy
+    int32_t *status;  // set to CUSCI_ERR_TIMEOUT if a copy never lands
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__host__ __device__ constexpr size_t stage_bytes(int slab, int mrow) {
+    return 16 + 2 * ((size_t)slab + (size_t)mrow) * 8;
+}
+
+__device__ __forceinline__ void stage_init(WarpStage &st, unsigned char *base, int slab, int mrow,
+                                           int lane, int32_t *status) {
+    st.bar = reinterpret_cast<uint64_t *>(base);
+    st.slab0 = reinterpret_cast<double *>(base + 16);
+    st.mrow0 = reinterpret_cast<uint64_t *>(st.slab0 + 2 * slab);
+    st.slab = slab;
+    st.mrow = mrow;
+    st.phase = 0;
+    st.next = 0;
+    st.status = status;
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(st.bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(st.bar + 1))
+                     : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+}
+
+// lane 0 issues the bulk copies of pair q's slab and mask row into buffer b
+__device__ __forceinline__ void stage_issue(WarpStage &st, const SysView &v, size_t q, int b,
+                                            int lane) {
+    __syncwarp();
+    if (lane == 0) {
+        const uint32_t bs = (uint32_t)v.slab * 8u, bm = (uint32_t)v.mrow * 8u;
+        const uint32_t bar = smem_addr(st.bar + b);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(bs + bm)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(smem_addr(st.slab0 + b * st.slab)),
+            "l"(v.T + q * v.slab), "r"(bs), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(smem_addr(st.mrow0 + b * st.mrow)),
+            "l"(v.mask + q * v.mrow), "r"(bm), "r"(bar)
+            : "memory");
+    }
+}
+
+// every lane waits (bounded) for buffer b, then flips its expected parity
+__device__ __forceinline__ void stage_wait(WarpStage &st, int b) {
+    const uint32_t bar = smem_addr(st.bar + b);
+    const uint32_t par = (st.phase >> b) & 1u;
+    uint32_t done = 0;
+    for (int tries = 0; tries < (1 << 22) && !done; tries++) {
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+            "selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar), "r"(par)
+            : "memory");
+    }
+    if (!done && st.status) *st.status = CUSCI_ERR_TIMEOUT;
+    st.phase ^= 1u << b;
+}
+
+// first occupied spin orbital above x (x = -1: the lowest), or -1
+template <int W>
+__device__ __forceinline__ int next_occ(const uint64_t (&d)[W], int x) {
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const int lo = 64 * w;
+        if (x >= lo + 63) continue;
+        uint64_t r = d[w];
+        if (x >= lo) r &= ~0ull << (x - lo + 1);
+        if (r) return lo + __ffsll((long long)r) - 1;
+    }
+    return -1;
+}
+
+// slab index of the occupied pair (i < j): kind 0 same spin, 1 opposite
+__device__ __forceinline__ size_t pair_index(int n, int i, int j) {
+    const int kind = ((i ^ j) & 1) ? 1 : 0;
+    return (size_t)(kind * n + (i >> 1)) * n + (j >> 1);
+}
+
 // Visits every kept entry of the coupled set of source s in canonical order.
 // emit(t, h, rank) is called by the lane that owns the entry: t is the target
 // determinant, h the signed FP64 element, rank its position in the source's
@@ -204,10 +311,14 @@ __device__ int64_t count_source(const SysView &v, const Src<W> &s, double eps, i
 // control flow); returns |C_s|.
 template <int W, class Emit>
 __device__ __forceinline__ int64_t visit_source(const SysView &v, const Src<W> &s, double eps,
-                                                int lane, Emit &emit) {
+                                                int lane, Emit &emit, WarpStage *stg = nullptr) {
     const int n = v.norb;
     const int nchunk = (n + 31) >> 5;
     int64_t pos = 0;
+    // prefetch the first occupied pair while the diagonal and singles run
+    const int i0 = next_occ<W>(s.d, -1);
+    const int j0 = i0 >= 0 ? next_occ<W>(s.d, i0) : -1;
+    if (stg && j0 >= 0) stage_issue(*stg, v, pair_index(n, i0, j0), stg->next, lane);
     // 1. diagonal
     {
         double hd = diagonal_value<W>(v, s);
@@ -225,7 +336,7 @@ __device__ __forceinline__ int64_t visit_source(const SysView &v, const Src<W> &
                 const int pa = lane + 32 * c;
                 bool keep = false;
                 double acc = 0.0;
-                if (pa < n && ((s.vir[sg] >> pa) & 1ull)) {
+                if (pa < n && ((sel2(s.vir, sg) >> pa) & 1ull)) {
                     acc = single_value<W>(v, s, i, pa);
                     keep = fabs(acc) > eps;
                 }
@@ -243,59 +354,97 @@ __device__ __forceinline__ int64_t visit_source(const SysView &v, const Src<W> &
                 pos += __popc(b);
             }
         }
-    // 3. doubles
+    // 3. doubles, one occupied pair (i < j) at a time in canonical order.
+    // Lane-constant side of b (lane owns spatial pb = lane + 32 c; W chunks
+    // cover norb <= 32 W): its bit in the target determinant, the parity of
+    // occupied orbitals below it, and the mask of lower b bits.
+    uint64_t bm[W][2][W];
+    uint32_t bpar[W][2];
+    uint64_t below[W];
 #pragma unroll
-    for (int wi = 0; wi < W; wi++)
-        for (uint64_t ri = s.d[wi]; ri; ri &= ri - 1) {
-            const int i = 64 * wi + __ffsll((long long)ri) - 1;
-            const int pi = i >> 1, si = i & 1;
-            const uint32_t ni = par_bit(s.par, i);
+    for (int c = 0; c < W; c++) {
+        const int pb = lane + 32 * c;
+        below[c] = pb == 0 ? 0ull : (~0ull >> (64 - pb));
 #pragma unroll
-            for (int wj = 0; wj < W; wj++) {
-                uint64_t rj = s.d[wj];
-                if (wj < wi) rj = 0;
-                else if (wj == wi) rj &= (i & 63) == 63 ? 0ull : (~0ull << ((i & 63) + 1));
-                for (; rj; rj &= rj - 1) {
-                    const int j = 64 * wj + __ffsll((long long)rj) - 1;
-                    const int pj = j >> 1, sj = j & 1;
-                    const int kind = (si == sj) ? 0 : 1;
-                    const size_t row0 = ((size_t)(kind * n + pi) * n + pj) * n;
-                    const uint64_t *__restrict__ mrow = v.mask + row0;
-                    const uint32_t nij = ni ^ par_bit(s.par, j) ^ 1u;
-                    uint64_t tij[W];
+        for (int sg = 0; sg < 2; sg++) {
+            const int b = 2 * pb + sg;
 #pragma unroll
-                    for (int q = 0; q < W; q++) tij[q] = s.d[q];
-                    flip_bit<W>(tij, i);
-                    flip_bit<W>(tij, j);
-                    for (uint64_t ra = s.vir[si]; ra; ra &= ra - 1) {
-                        const int pa = __ffsll((long long)ra) - 1;
-                        const uint64_t m = __ldg(mrow + pa) & s.vir[sj];
-                        if (m == 0) continue;
-                        const int a = 2 * pa + si;
-                        const uint32_t cija =
-                            nij ^ par_bit(s.par, a) ^ (uint32_t)(i < a) ^ (uint32_t)(j < a);
-                        const double *__restrict__ trow = v.T + (row0 + pa) * n;
-                        for (int c = 0; c < nchunk; c++) {
-                            const int pb = lane + 32 * c;
-                            if (pb < n && ((m >> pb) & 1ull)) {
-                                const int b = 2 * pb + sj;
-                                const int64_t p =
-                                    pos + __popcll(m & ((pb == 0) ? 0ull : (~0ull >> (64 - pb))));
-                                const uint32_t odd = cija ^ par_bit(s.par, b) ^ (uint32_t)(i < b) ^
-                                                     (uint32_t)(j < b) ^ (uint32_t)(b < a);
-                                uint64_t t[W];
+            for (int w = 0; w < W; w++)
+                bm[c][sg][w] = ((b >> 6) == w) ? (1ull << (b & 63)) : 0ull;
+            bpar[c][sg] = (uint32_t)((s.par[sg] >> pb) & 1ull);
+        }
+    }
+    int cur = stg ? stg->next : 0;
+    for (int i = i0, j = j0; j >= 0;) {
+        int ni = i, nj = next_occ<W>(s.d, j);
+        if (nj < 0) {
+            ni = next_occ<W>(s.d, i);
+            nj = ni >= 0 ? next_occ<W>(s.d, ni) : -1;
+        }
+        const int si = i & 1, sj = j & 1;
+        const size_t q = pair_index(n, i, j);
+        const double *__restrict__ slab;
+        const uint64_t *__restrict__ mrow;
+        if (stg) {
+            if (nj >= 0) stage_issue(*stg, v, pair_index(n, ni, nj), cur ^ 1, lane);
+            stage_wait(*stg, cur);
+            slab = stg->slab0 + cur * stg->slab;
+            mrow = stg->mrow0 + cur * stg->mrow;
+        } else {
+            slab = v.T + q * v.slab;
+            mrow = v.mask + q * v.mrow;
+        }
+        const uint32_t nij = par_bit(s.par, i) ^ par_bit(s.par, j) ^ 1u;
+        uint64_t tij[W];
 #pragma unroll
-                                for (int q = 0; q < W; q++) t[q] = tij[q];
-                                flip_bit<W>(t, a);
-                                flip_bit<W>(t, b);
-                                emit(t, flip_sign(__ldg(trow + pb), odd), p);
-                            }
-                        }
-                        pos += __popcll(m);
-                    }
+        for (int w = 0; w < W; w++) tij[w] = s.d[w];
+        flip_bit<W>(tij, i);
+        flip_bit<W>(tij, j);
+        // per pair, per lane: parity of b's position relative to i and j
+        uint32_t lij[W];
+        uint64_t bmj[W][W];
+#pragma unroll
+        for (int c = 0; c < W; c++) {
+            const int b = 2 * (lane + 32 * c) + sj;
+            lij[c] = sel2(bpar[c], sj) ^ (uint32_t)(i < b) ^ (uint32_t)(j < b);
+#pragma unroll
+            for (int w = 0; w < W; w++) bmj[c][w] = sj ? bm[c][1][w] : bm[c][0][w];
+        }
+        for (uint64_t ra = sel2(s.vir, si); ra; ra &= ra - 1) {
+            const int pa = __ffsll((long long)ra) - 1;
+            const uint64_t m = (stg ? mrow[pa] : __ldg(mrow + pa)) & sel2(s.vir, sj);
+            if (m == 0) continue;
+            const int a = 2 * pa + si;
+            const uint32_t cija = nij ^ par_bit(s.par, a) ^ (uint32_t)(i < a) ^ (uint32_t)(j < a);
+            uint64_t tija[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) tija[w] = tij[w];
+            flip_bit<W>(tija, a);
+            const double *__restrict__ trow = slab + pa * n;
+#pragma unroll
+            for (int c = 0; c < W; c++) {
+                const int pb = lane + 32 * c;
+                if ((m >> pb) & 1ull) {
+                    const int b = 2 * pb + sj;
+                    const int64_t p = pos + __popcll(m & below[c]);
+                    const uint32_t odd = cija ^ lij[c] ^ (uint32_t)(b < a);
+                    uint64_t t[W];
+#pragma unroll
+                    for (int w = 0; w < W; w++) t[w] = tija[w] ^ bmj[c][w];
+                    const double val = stg ? trow[pb] : __ldg(trow + pb);
+                    emit(t, flip_sign(val, odd), p);
                 }
             }
+            pos += __popcll(m);
         }
+        if (stg) {
+            __syncwarp();
+            cur ^= 1;
+        }
+        i = ni;
+        j = nj;
+    }
+    if (stg) stg->next = cur;
     return pos;
 }
 

@@ -34,43 +34,40 @@ __global__ void build_small_tables(int n, const double *__restrict__ h2, double 
     }
 }
 
-// T[kind][pi][pj][pa][pb]
-__global__ void build_T(int n, const double *__restrict__ h2, double *T) {
-    const size_t n4 = (size_t)n * n * n * n;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < 2 * n4;
+// T: slab q = (kind*n + pi)*n + pj of `slab` doubles, element pa*n + pb
+__global__ void build_T(int n, int slab, const double *__restrict__ h2, double *T) {
+    const size_t total = 2 * (size_t)n * n * slab;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
-        size_t r = t;
-        int pb = (int)(r % n); r /= n;
-        int pa = (int)(r % n); r /= n;
-        int pj = (int)(r % n); r /= n;
-        int pi = (int)(r % n); r /= n;
-        int kind = (int)r;
-        double direct = h2[((size_t)(pa * n + pi) * n + pb) * n + pj];  // (ai|bj)
-        double v;
-        if (kind == 1) {
-            v = direct;
-        } else if (pi < pj && pa < pb) {
-            double exch = h2[((size_t)(pa * n + pj) * n + pb) * n + pi];  // (aj|bi)
-            v = __dsub_rn(direct, exch);
-        } else {
-            v = 0.0;
+        const size_t q = t / slab;
+        const int e = (int)(t % slab);
+        double v = 0.0;
+        if (e < n * n) {
+            const int pa = e / n, pb = e % n;
+            const int pj = (int)(q % n), pi = (int)((q / n) % n), kind = (int)(q / ((size_t)n * n));
+            const double direct = h2[((size_t)(pa * n + pi) * n + pb) * n + pj];  // (ai|bj)
+            if (kind == 1) {
+                v = direct;
+            } else if (pi < pj && pa < pb) {
+                const double exch = h2[((size_t)(pa * n + pj) * n + pb) * n + pi];  // (aj|bi)
+                v = __dsub_rn(direct, exch);
+            }
         }
         T[t] = v;
     }
 }
 
-__global__ void build_masks(int n, const double *__restrict__ T, double eps, uint64_t *bits) {
-    const size_t rows = 2 * (size_t)n * n * n;
+__global__ void build_masks(int n, int slab, int mrow, const double *__restrict__ T, double eps,
+                            uint64_t *bits) {
+    const size_t rows = 2 * (size_t)n * n * mrow;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < rows;
          t += (size_t)gridDim.x * blockDim.x) {
-        size_t r = t;
-        int pa = (int)(r % n); r /= n;
-        int pj = (int)(r % n); r /= n;
-        int pi = (int)(r % n); r /= n;
-        int kind = (int)r;
-        const double *row = T + t * n;
+        const size_t q = t / mrow;
+        const int pa = (int)(t % mrow);
+        const int pj = (int)(q % n), pi = (int)((q / n) % n), kind = (int)(q / ((size_t)n * n));
         uint64_t m = 0;
-        if (kind == 1 || pi < pj) {
+        if (pa < n && (kind == 1 || pi < pj)) {
+            const double *row = T + q * slab + (size_t)pa * n;
             for (int pb = (kind == 0 ? pa + 1 : 0); pb < n; pb++)
                 if (fabs(row[pb]) > eps) m |= 1ull << pb;
         }
@@ -104,14 +101,14 @@ cusci_status masks_for(cusci_system *sys, double eps, cudaStream_t stream, const
     }
     MaskSlot &m = sys->masks[victim];
     const int n = sys->norb;
-    const size_t rows = 2 * (size_t)n * n * n;
+    const size_t rows = 2 * (size_t)n * n * sys->mrow;
     if (!m.bits) {
         cudaError_t e = cudaMalloc(&m.bits, rows * sizeof(uint64_t));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(screening masks)");
     }
     int blocks = (int)((rows + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    build_masks<<<blocks, 256, 0, stream>>>(n, sys->T, eps, m.bits);
+    build_masks<<<blocks, 256, 0, stream>>>(n, sys->slab, sys->mrow, sys->T, eps, m.bits);
     CUSCI_LAUNCHED(1, "build_masks");
     m.eps = eps;
     m.valid = true;
@@ -140,6 +137,8 @@ extern "C" cusci_status cusci_system_create(int norb, int n_alpha, int n_beta, c
     if (!s) return fail(CUSCI_ERR_OOM, "cusci_system_create: host allocation");
     s->norb = norb; s->n_alpha = n_alpha; s->n_beta = n_beta;
     s->M = 2 * norb; s->W = (2 * norb + 63) / 64; s->ecore = ecore;
+    s->slab = norb * norb + ((norb * norb) & 1);
+    s->mrow = norb + (norb & 1);
     cudaGetDevice(&s->device);
 
     const size_t n = norb, n2 = n * n, n3 = n2 * n, n4 = n3 * n;
@@ -157,16 +156,16 @@ extern "C" cusci_status cusci_system_create(int norb, int n_alpha, int n_beta, c
     ALLOC(s->K, n2);
     ALLOC(s->S1, n3);
     ALLOC(s->S2, n3);
-    ALLOC(s->T, 2 * n4);
+    ALLOC(s->T, 2 * n2 * (size_t)s->slab);
     ALLOC(d_h2, n4);
 #undef ALLOC
     e = cudaMemcpy(s->h1, h1, n2 * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_h2, h2, n4 * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        int blocks = (int)((2 * n4 + 255) / 256);
+        int blocks = (int)((2 * n2 * (size_t)s->slab + 255) / 256);
         if (blocks > 8192) blocks = 8192;
         build_small_tables<<<(int)((n3 + 255) / 256), 256>>>(norb, d_h2, s->J, s->K, s->S1, s->S2);
-        build_T<<<blocks, 256>>>(norb, d_h2, s->T);
+        build_T<<<blocks, 256>>>(norb, s->slab, d_h2, s->T);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);

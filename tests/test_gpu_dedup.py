@@ -94,3 +94,55 @@ def test_workspace_too_small_is_an_error():
                              ctypes.c_void_p(inv.data_ptr()), 4, ctypes.c_void_p(nu.data_ptr()),
                              None, None, None)
         cusci._check(rc, "cusci_dedup")
+
+
+# ---- sample-sort path (taken for >= 2^22 keys whose sort key fits 42 bits)
+
+def test_sample_sort_rank_keys_vs_oracle():
+    s, td = coupled_keys("mid", 400)          # ~6.7M entries, ranks of 41 bits
+    assert td.shape[0] >= (1 << 22)
+    compare(td, 2 * s.norb, s.n_alpha + s.n_beta)
+
+
+def test_sample_sort_raw_keys_vs_oracle():
+    rng = np.random.default_rng(7)
+    base = rng.integers(0, 1 << 40, size=600_000).astype(np.uint64)
+    keys = base[rng.integers(0, base.size, size=5_000_000)].reshape(-1, 1)
+    compare(keys, 40, -1)
+
+
+def test_sample_sort_two_word_keys_vs_oracle():
+    norb = 33                                  # 66 spin orbitals -> two words
+    h1, h2 = synth.integrals(norb, seed=4)
+    dets = synth.sample_dets(norb, 3, 3, 420, seed=5)
+    off, td, hv = O.OracleSystem(norb, 3, 3, h1, h2).gen(dets, -1.0)
+    assert td.shape[0] >= (1 << 22) and td.shape[1] == 2
+    compare(td, 2 * norb, 6)
+
+
+def test_sample_sort_heavy_hitter_leaf():
+    """One key repeated far beyond a shared-memory leaf (the global-memory leaf path)."""
+    rng = np.random.default_rng(8)
+    keys = rng.integers(0, 1 << 36, size=4_500_000).astype(np.uint64)
+    keys[rng.choice(keys.size, 1_500_000, replace=False)] = 123456789
+    compare(keys.reshape(-1, 1), 36, -1)
+
+
+def test_full_size_dedup_properties():
+    """The benchmark's input (100k sources, 1.675e9 entries): the distinct list is
+    strictly ascending, gathers back to every key through the inverse, and every
+    distinct key is used; together these fix the answer."""
+    s = synth.config_system("mid")
+    sysd = cusci.System.of(s)
+    off, od, oh, st = cusci.coupled(sysd, to_dev(s.dets), s.eps)
+    del oh
+    u, inv, nu = cusci.dedup(od, 2 * s.norb, s.n_alpha + s.n_beta)
+    assert nu > 0
+    assert bool((u[1:, 0] > u[:-1, 0]).all())                 # 52-bit keys: int64 order is exact
+    chunk = 1 << 28
+    for a in range(0, od.shape[0], chunk):
+        b = min(od.shape[0], a + chunk)
+        assert bool((u[inv[a:b].long(), 0] == od[a:b, 0]).all())
+    used = torch.zeros(nu, dtype=torch.bool, device="cuda")
+    used[inv.long()] = True
+    assert bool(used.all())
