@@ -251,11 +251,22 @@ def run_ours(args):
     dom_gbs, dom_bytes, dom_ms = ((dedup_gbs, dedup_bytes, dedup_ms) if dedup_ms >= gen_ms
                                   else (gen_gbs, gen_bytes, gen_ms))
 
+    # release the timed step's buffers before the other measurements
+    del out_d, out_h, dd_ws, uniq, inv, flush
+    torch.cuda.empty_cache()
+
     # end to end through the public API with host buffers
     e2e = run_e2e(args, s, sysd, dev) if args.e2e else None
+    torch.cuda.empty_cache()
 
     # energy forward + adjoint on the 200k selected set
     energy = run_energy(args, dev) if args.energy else None
+
+    torch.cuda.empty_cache()
+    stream_res = run_stream(args, dev) if args.stream else None
+    torch.cuda.empty_cache()
+    batch_res = run_batched(args, dev) if args.batched else None
+    torch.cuda.empty_cache()
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = run_cpu_baseline(args) if (rank == 0 and ws == 1 and args.cpu_baseline) else None
@@ -292,6 +303,10 @@ def run_ours(args):
             line["energy"] = energy
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if stream_res is not None:
+            line["streaming"] = stream_res
+        if batch_res is not None:
+            line["batched"] = batch_res
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -384,6 +399,78 @@ def run_energy(args, dev):
                         "seeded 256-256 tanh MLP"}
 
 
+def run_stream(args, dev):
+    """Large two-word system (120 spin orbitals, 10a+10b, 20k sources, eps 1e-6)
+    through mini-batches of a bounded pool, coupled lists offloaded to pinned
+    host memory."""
+    import torch
+
+    from paper_2604_15768_gb300 import cusci, synth
+    s = synth.config_system("large", n_dets=args.stream_sources)
+    sysd = cusci.System.of(s)
+    batch = args.stream_batch
+    ucap = args.stream_unique_cap
+    # host capacity from the counts (one untimed count pass)
+    d = cusci.dets_to_device(s.dets, dev)
+    total = int(cusci.count_coupled(sysd, d, s.eps).sum().item())
+    del d
+    hcap = total
+    pool = torch.empty(cusci.stream_pool_bytes(sysd, s.dets.shape[0], batch, ucap),
+                       dtype=torch.uint8, device=dev)
+    res = None
+    times = []
+    for it in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = cusci.stream_gen_dedup(sysd, s.dets, s.eps, batch, ucap, host_capacity=hcap,
+                                     pool=pool)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    off, hd, hh, uniq, st = res
+    t = min(times[1:]) if len(times) > 1 else times[0]
+    return {"entries_per_s": st["total"] / t, "ms": t * 1e3, "entries": st["total"],
+            "unique": int(uniq.shape[0]), "batches": st["batches"],
+            "batch_entries": batch, "pool_bytes": st["pool_bytes"],
+            "pool_peak_bytes": st["pool_peak"], "batch_region_bytes": 2 * batch * 24,
+            "coupled_set_bytes": st["total"] * 24, "d2h_bytes": st["d2h_bytes"],
+            "d2h_gbs": st["d2h_bytes"] / t / 1e9,
+            "workload": f"large: 120 spin orbitals (2 words), 10a+10b, {s.dets.shape[0]} sources, "
+                        "eps 1e-6; host sources in, host coupled lists + device distinct set out"}
+
+
+def run_batched(args, dev):
+    """64 independent systems of uneven size in one persistent launch per pass,
+    per-system de-duplication, the whole sequence replayed from a CUDA graph."""
+    import torch
+
+    from paper_2604_15768_gb300 import cusci, synth
+    t0 = time.perf_counter()
+    systems = synth.batched_systems(64, scale=args.batch_scale)
+    t_synth = time.perf_counter() - t0
+    b = cusci.Batch(systems, [x.dets for x in systems], 1e-8, chunk=8)
+    b.plan()
+    chunk, _ = b.autotune()
+    b.capture()
+    for _ in range(2):
+        b.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        b.replay()
+        z.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(z))
+    ms = float(np.median(ts))
+    return {"entries_per_s": b.total / (ms * 1e-3), "ms": ms, "entries": b.total,
+            "systems": len(systems), "sources": int(b.n), "chunk": int(chunk),
+            "unique_total": int(b.n_unique.sum().item()), "synth_s": t_synth,
+            "workload": f"64 systems, norb 10..50, 4..16 electrons, sources "
+                        f"floor(logU(1e3,5e4) x {args.batch_scale}), eps 1e-8, graph replay "
+                        "of count+scan+fill+per-system dedup"}
+
+
 def run_cpu_baseline(args):
     from oracle import oracle as O
     from paper_2604_15768_gb300 import synth
@@ -411,6 +498,12 @@ def main(argv=None):
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-energy", dest="energy", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-stream", dest="stream", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--stream-sources", type=int, default=20_000)
+    ap.add_argument("--stream-batch", type=int, default=16_000_000)
+    ap.add_argument("--stream-unique-cap", type=int, default=400_000_000)
+    ap.add_argument("--batch-scale", type=float, default=0.25)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -187,6 +187,67 @@ cusci_status cusci_energy_bwd(const cusci_system *sys, const uint64_t *d_S, int6
                               const double *d_grad_out, double *d_grad, void *d_ws,
                               size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------ streaming
+ * Generation + de-duplication in mini-batches out of a caller-owned device
+ * pool (Sec. 4.3: mini-batch execution, compute/transfer overlap, Stage 1
+ * offload of the original coupled set to host memory).
+ * h_dets: host [n][W] sources.  d_pool: device memory of pool_bytes, 256-byte
+ * aligned, at least cusci_stream_pool_bytes(); the library uses nothing else
+ * on the device.  batch_entries: capacity of one mini-batch (two are in flight:
+ * one filled while the other is copied out); every single source's list must
+ * fit one batch.  h_offsets: host int64[n+1], receives the CSR offsets of the
+ * whole coupled set.  h_out_dets / h_out_h: host sinks (pinned for overlap)
+ * of host_capacity entries receiving the coupled lists in canonical order, or
+ * both NULL to skip the offload.  d_unique: device [unique_capacity][W],
+ * receives the sorted distinct targets of all batches; *h_n_unique their
+ * number.  h_stats (nullable, host int64[4]): total entries, batches, peak pool
+ * bytes used, bytes offloaded.  Synchronous (returns when everything landed).
+ * Errors: CUSCI_ERR_OOM (pool or sinks too small, or a source longer than a
+ * batch), CUSCI_ERR_OVERFLOW (more distinct keys than unique_capacity),
+ * CUSCI_ERR_TIMEOUT (a bounded wait in the hash set gave up),
+ * CUSCI_ERR_UNSUPPORTED (64 or more electrons). */
+cusci_status cusci_stream_pool_bytes(const cusci_system *sys, int64_t n_sources,
+                                     int64_t batch_entries, int64_t unique_capacity,
+                                     size_t *bytes);
+cusci_status cusci_stream_gen_dedup(const cusci_system *sys, const uint64_t *h_dets, int64_t n,
+                                    double eps, void *d_pool, size_t pool_bytes,
+                                    int64_t batch_entries, int64_t *h_offsets,
+                                    uint64_t *h_out_dets, double *h_out_h,
+                                    int64_t host_capacity, uint64_t *d_unique,
+                                    int64_t unique_capacity, int64_t *h_n_unique,
+                                    int64_t *h_stats, void *stream);
+
+/* ------------------------------------------------------------------ batched systems
+ * Many independent systems in one persistent launch (the persistent
+ * grid-stride kernel of Algorithm 1, extended over systems): warps pull
+ * (system, source chunk) work items, largest estimated cost first, from an
+ * atomic counter.  Sources of every system are stored as two words per
+ * determinant, systems back to back in the order given (one-word systems carry
+ * a zero high word); targets are written the same way into one CSR over all
+ * sources.  cusci_batch_create: systems stay owned by the caller and must
+ * outlive the batch; h_sources[k] = number of sources of system k; chunk =
+ * sources per work item (cusci_batch_set_chunk changes it).  The first count
+ * or gen call at a new eps builds the systems' screening masks and
+ * synchronizes the stream; later calls at the same eps are plain asynchronous
+ * launches (capturable in a CUDA graph).  Per-system de-duplication is
+ * cusci_dedup on each system's slice of the targets. */
+typedef struct cusci_batch cusci_batch;
+cusci_status cusci_batch_create(const cusci_system *const *systems, int n_systems,
+                                const int64_t *h_sources, int chunk, cusci_batch **out);
+void cusci_batch_destroy(cusci_batch *batch);
+cusci_status cusci_batch_set_chunk(cusci_batch *batch, int chunk);
+int64_t cusci_batch_sources(const cusci_batch *batch);
+/* d_dets: device [total sources][2]; d_counts: device int64[total sources]. */
+cusci_status cusci_batch_count(cusci_batch *batch, const uint64_t *d_dets, double eps,
+                               int64_t *d_counts, void *stream);
+/* d_offsets: exclusive scan of the counts (total sources + 1); d_out_dets:
+ * device [total][2], 16-byte aligned; d_out_h: device double[total];
+ * d_status (nullable): CUSCI_ERR_OVERFLOW if offsets and regenerated counts
+ * disagree. */
+cusci_status cusci_batch_gen(cusci_batch *batch, const uint64_t *d_dets, double eps,
+                             const int64_t *d_offsets, uint64_t *d_out_dets, double *d_out_h,
+                             int32_t *d_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

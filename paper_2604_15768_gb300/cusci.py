@@ -55,6 +55,15 @@ _PROTOS = {
     "cusci_check_dets": (_I, [_P, _P, _I64, _P, _P]),
     "cusci_dedup_workspace": (_I, [_I64, _I, _I, _I, ctypes.POINTER(_SZ)]),
     "cusci_dedup": (_I, [_P, _I64, _I, _I, _I, _P, _SZ, _P, _P, _I, _P, _P, _P, _P]),
+    "cusci_stream_pool_bytes": (_I, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
+    "cusci_stream_gen_dedup": (_I, [_P, _P, _I64, _D, _P, _SZ, _I64, _P, _P, _P, _I64, _P, _I64,
+                                    _P, _P, _P]),
+    "cusci_batch_create": (_I, [_P, _I, _P, _I, ctypes.POINTER(_P)]),
+    "cusci_batch_destroy": (None, [_P]),
+    "cusci_batch_set_chunk": (_I, [_P, _I]),
+    "cusci_batch_sources": (_I64, [_P]),
+    "cusci_batch_count": (_I, [_P, _P, _D, _P, _P]),
+    "cusci_batch_gen": (_I, [_P, _P, _D, _P, _P, _P, _P, _P]),
     "cusci_energy_workspace": (_I, [_P, _I64, ctypes.POINTER(_SZ)]),
     "cusci_energy_fwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _SZ, _P, _P]),
     "cusci_energy_bwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -262,6 +271,51 @@ def coupled(sys: System, dets: torch.Tensor, eps: float, stream=None):
     return offsets, out_d, out_h, status
 
 
+def stream_pool_bytes(sys: System, n_sources: int, batch_entries: int,
+                      unique_capacity: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().cusci_stream_pool_bytes(sys.handle, int(n_sources), int(batch_entries),
+                                          int(unique_capacity), ctypes.byref(b)),
+           "cusci_stream_pool_bytes")
+    return b.value
+
+
+def stream_gen_dedup(sys: System, dets: np.ndarray, eps: float, batch_entries: int,
+                     unique_capacity: int, host_capacity: int | None = None, offload=True,
+                     pool=None, stream=None):
+    """Mini-batched generation + de-duplication (host sources in, host coupled
+    lists and device distinct set out).  Returns (offsets, host_dets, host_h,
+    unique, stats) with host arrays pinned."""
+    dets = np.ascontiguousarray(dets, dtype=np.uint64).reshape(-1, sys.W)
+    n = dets.shape[0]
+    h_src = torch.from_numpy(dets.view(np.int64)).pin_memory()
+    need = stream_pool_bytes(sys, n, batch_entries, unique_capacity)
+    if pool is None or pool.numel() < need:
+        pool = torch.empty(need, dtype=torch.uint8, device="cuda")
+    offsets = np.zeros(n + 1, dtype=np.int64)
+    hd = hh = None
+    cap = 0
+    if offload:
+        cap = int(host_capacity)
+        hd = torch.empty((max(cap, 1), sys.W), dtype=torch.int64).pin_memory()
+        hh = torch.empty(max(cap, 1), dtype=torch.float64).pin_memory()
+    uniq = torch.empty((unique_capacity, sys.W), dtype=torch.int64, device="cuda")
+    nu = ctypes.c_int64(0)
+    stats = np.zeros(4, dtype=np.int64)
+    _check(load().cusci_stream_gen_dedup(
+        sys.handle, ctypes.c_void_p(h_src.data_ptr()), n, float(eps), _ptr(pool), pool.numel(),
+        int(batch_entries), offsets.ctypes.data_as(_P), _ptr(hd), _ptr(hh), cap, _ptr(uniq),
+        int(unique_capacity), ctypes.byref(nu), stats.ctypes.data_as(_P), _stream(stream)),
+        "cusci_stream_gen_dedup")
+    total = int(offsets[-1])
+    out_d = hd[:total] if offload else None
+    out_h = hh[:total] if offload else None
+    return offsets, out_d, out_h, uniq[:nu.value], {"total": int(stats[0]), "batches": int(stats[1]),
+                                                     "pool_peak": int(stats[2]),
+                                                     "d2h_bytes": int(stats[3]),
+                                                     "pool_bytes": int(pool.numel())}
+
+
 def energy_workspace(sys: System, nS: int) -> int:
     ws = ctypes.c_size_t()
     _check(load().cusci_energy_workspace(sys.handle, int(nS), ctypes.byref(ws)),
@@ -331,3 +385,129 @@ class Energy(torch.autograd.Function):
             psi, S, E, n2, hp = ctx.saved_tensors
         grad = energy_bwd(ctx.system, S, psi, ctx.eps, E, n2, hpsi=hp, grad_out=g)
         return grad, None, None, None, None
+
+
+class Batch:
+    """Many systems generated in one persistent launch (plus per-system dedup).
+
+    ``plan()`` runs one untimed count/scan to size every buffer; ``run()``
+    issues count -> scan -> fill -> per-system dedup on the current stream with
+    no host synchronisation, so it can be captured with ``capture()`` in a CUDA
+    graph and replayed with ``replay()``.
+    """
+
+    def __init__(self, systems, dets_list, eps, chunk=8):
+        lib = load()
+        self.systems = [System.of(s) for s in systems]
+        self.eps = float(eps)
+        n_src = np.array([d.shape[0] for d in dets_list], dtype=np.int64)
+        handles = (_P * len(self.systems))(*[s.handle.value for s in self.systems])
+        h = ctypes.c_void_p()
+        _check(lib.cusci_batch_create(handles, len(self.systems), n_src.ctypes.data_as(_P),
+                                      int(chunk), ctypes.byref(h)), "cusci_batch_create")
+        self._h = h
+        self._handles = handles
+        self.chunk = int(chunk)
+        self.src_begin = np.concatenate([[0], np.cumsum(n_src)])
+        packed = np.zeros((int(self.src_begin[-1]), 2), dtype=np.uint64)
+        for k, d in enumerate(dets_list):
+            d = np.ascontiguousarray(d, dtype=np.uint64)
+            packed[self.src_begin[k]:self.src_begin[k + 1], :d.shape[1]] = d
+        self.d_src = dets_to_device(packed)
+        self.n = packed.shape[0]
+        self.graph = None
+
+    def set_chunk(self, chunk):
+        _check(load().cusci_batch_set_chunk(self._h, int(chunk)), "cusci_batch_set_chunk")
+        self.chunk = int(chunk)
+
+    def count(self, counts, stream=None):
+        _check(load().cusci_batch_count(self._h, _ptr(self.d_src), self.eps, _ptr(counts),
+                                        _stream(stream)), "cusci_batch_count")
+
+    def gen(self, offsets, out_d, out_h, status=None, stream=None):
+        _check(load().cusci_batch_gen(self._h, _ptr(self.d_src), self.eps, _ptr(offsets),
+                                      _ptr(out_d), _ptr(out_h), _ptr(status), _stream(stream)),
+               "cusci_batch_gen")
+
+    def plan(self):
+        dev = self.d_src.device
+        self.counts = torch.empty(self.n, dtype=torch.int64, device=dev)
+        self.count(self.counts)
+        self.scan_ws = torch.empty(scan_workspace(self.n), dtype=torch.uint8, device=dev)
+        self.offsets = exclusive_scan(self.counts, workspace=self.scan_ws)
+        off = self.offsets.cpu().numpy()
+        self.entry_begin = off[self.src_begin]
+        self.total = int(off[-1])
+        self.out_d = torch.empty((max(self.total, 1), 2), dtype=torch.int64, device=dev)
+        self.out_h = torch.empty(max(self.total, 1), dtype=torch.float64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        ws = 1
+        self.dd = []
+        for k, s in enumerate(self.systems):
+            m = int(self.entry_begin[k + 1] - self.entry_begin[k])
+            ws = max(ws, dedup_workspace(max(m, 1), 2, s.M, s.n_alpha + s.n_beta))
+        self.dd_ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.unique = torch.empty((max(self.total, 1), 2), dtype=torch.int64, device=dev)
+        self.inverse = torch.empty(max(self.total, 1), dtype=torch.int32, device=dev)
+        self.n_unique = torch.zeros(len(self.systems), dtype=torch.int64, device=dev)
+        return self.total
+
+    def run(self, stream=None):
+        self.count(self.counts, stream)
+        exclusive_scan(self.counts, out=self.offsets, workspace=self.scan_ws, stream=stream)
+        self.gen(self.offsets, self.out_d, self.out_h, self.status, stream)
+        for k, s in enumerate(self.systems):
+            a, b = int(self.entry_begin[k]), int(self.entry_begin[k + 1])
+            if b == a:
+                continue
+            dedup_into(self.out_d[a:b], s.M, s.n_alpha + s.n_beta, self.unique[a:b],
+                       self.inverse[a:b], self.n_unique[k:k + 1], self.dd_ws, stream=stream)
+
+    def autotune(self, candidates=(1, 2, 4, 8, 16, 32, 64), reps=2):
+        """Pick the work-item size (sources per item) with the fastest fill launch."""
+        best = None
+        for c in candidates:
+            self.set_chunk(c)
+            self.gen(self.offsets, self.out_d, self.out_h, self.status)
+            torch.cuda.synchronize()
+            t = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                self.gen(self.offsets, self.out_d, self.out_h, self.status)
+                b.record()
+                torch.cuda.synchronize()
+                t.append(a.elapsed_time(b))
+            ms = min(t)
+            if best is None or ms < best[1]:
+                best = (c, ms)
+        self.set_chunk(best[0])
+        return best
+
+    def capture(self):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(stream=s)          # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _LIB is not None:
+            _LIB.cusci_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
