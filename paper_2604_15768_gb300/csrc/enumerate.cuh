@@ -298,6 +298,28 @@ __device__ __forceinline__ int next_occ(const uint64_t (&d)[W], int x) {
     return -1;
 }
 
+// position of the n-th (0-based) set bit of x; n < popcount(x) (else some
+// position in 0..31 / 0..63, never out of range)
+__device__ __forceinline__ int select32(uint32_t x, int n) {
+    int pos = 0, c;
+    c = __popc(x & 0xFFFFu);
+    if (n >= c) { n -= c; pos += 16; x >>= 16; }
+    c = __popc(x & 0xFFu);
+    if (n >= c) { n -= c; pos += 8; x >>= 8; }
+    c = __popc(x & 0xFu);
+    if (n >= c) { n -= c; pos += 4; x >>= 4; }
+    c = __popc(x & 0x3u);
+    if (n >= c) { n -= c; pos += 2; x >>= 2; }
+    if (n >= (int)(x & 1u)) pos += 1;
+    return pos;
+}
+
+__device__ __forceinline__ int select64(uint64_t x, int n) {
+    const uint32_t lo = (uint32_t)x;
+    const int cl = __popc(lo);
+    return n < cl ? select32(lo, n) : 32 + select32((uint32_t)(x >> 32), n - cl);
+}
+
 // slab index of the occupied pair (i < j): kind 0 same spin, 1 opposite
 __device__ __forceinline__ size_t pair_index(int n, int i, int j) {
     const int kind = ((i ^ j) & 1) ? 1 : 0;
@@ -355,25 +377,12 @@ __device__ __forceinline__ int64_t visit_source(const SysView &v, const Src<W> &
             }
         }
     // 3. doubles, one occupied pair (i < j) at a time in canonical order.
-    // Lane-constant side of b (lane owns spatial pb = lane + 32 c; W chunks
-    // cover norb <= 32 W): its bit in the target determinant, the parity of
-    // occupied orbitals below it, and the mask of lower b bits.
-    uint64_t bm[W][2][W];
-    uint32_t bpar[W][2];
-    uint64_t below[W];
-#pragma unroll
-    for (int c = 0; c < W; c++) {
-        const int pb = lane + 32 * c;
-        below[c] = pb == 0 ? 0ull : (~0ull >> (64 - pb));
-#pragma unroll
-        for (int sg = 0; sg < 2; sg++) {
-            const int b = 2 * pb + sg;
-#pragma unroll
-            for (int w = 0; w < W; w++)
-                bm[c][sg][w] = ((b >> 6) == w) ? (1ull << (b & 63)) : 0ull;
-            bpar[c][sg] = (uint32_t)((s.par[sg] >> pb) & 1ull);
-        }
-    }
+    // Per pair the surviving (a, b) are expanded across the warp: lanes first
+    // take rows (virtual a of i's spin, ascending, 32 per group) and prefix-sum
+    // their survivor counts; then every lane takes one output slot k, finds its
+    // row by a search over the lanes' prefix sums and its b as the
+    // (k - prefix)-th set bit of the row's mask.  All lanes stay busy whatever
+    // the mask density.
     int cur = stg ? stg->next : 0;
     for (int i = i0, j = j0; j >= 0;) {
         int ni = i, nj = next_occ<W>(s.d, j);
@@ -400,42 +409,64 @@ __device__ __forceinline__ int64_t visit_source(const SysView &v, const Src<W> &
         for (int w = 0; w < W; w++) tij[w] = s.d[w];
         flip_bit<W>(tij, i);
         flip_bit<W>(tij, j);
-        // per pair, per lane: parity of b's position relative to i and j
-        uint32_t lij[W];
-        uint64_t bmj[W][W];
+        const uint64_t virj = sel2(s.vir, sj);
+        const uint64_t parj = sel2(s.par, sj);
+        for (uint64_t vs = sel2(s.vir, si); vs;) {
+            // row of this lane: the lane-th remaining virtual a
+            const int rows = __popcll(vs) < 32 ? __popcll(vs) : 32;
+            int pa = -1;
+            uint64_t m = 0;
+            if (lane < rows) {
+                pa = select64(vs, lane);
+                m = (stg ? mrow[pa] : __ldg(mrow + pa)) & virj;
+            }
+            const uint32_t cnt = (uint32_t)__popcll(m);
+            uint32_t incl = cnt;
 #pragma unroll
-        for (int c = 0; c < W; c++) {
-            const int b = 2 * (lane + 32 * c) + sj;
-            lij[c] = sel2(bpar[c], sj) ^ (uint32_t)(i < b) ^ (uint32_t)(j < b);
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t excl = incl - cnt;
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            const int a_l = 2 * pa + si;
+            const uint32_t cija_l =
+                nij ^ (pa >= 0 ? par_bit(s.par, a_l) : 0u) ^ (uint32_t)(i < a_l) ^ (uint32_t)(j < a_l);
+            for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                int r = 0;
 #pragma unroll
-            for (int w = 0; w < W; w++) bmj[c][w] = sj ? bm[c][1][w] : bm[c][0][w];
-        }
-        for (uint64_t ra = sel2(s.vir, si); ra; ra &= ra - 1) {
-            const int pa = __ffsll((long long)ra) - 1;
-            const uint64_t m = (stg ? mrow[pa] : __ldg(mrow + pa)) & sel2(s.vir, sj);
-            if (m == 0) continue;
-            const int a = 2 * pa + si;
-            const uint32_t cija = nij ^ par_bit(s.par, a) ^ (uint32_t)(i < a) ^ (uint32_t)(j < a);
-            uint64_t tija[W];
-#pragma unroll
-            for (int w = 0; w < W; w++) tija[w] = tij[w];
-            flip_bit<W>(tija, a);
-            const double *__restrict__ trow = slab + pa * n;
-#pragma unroll
-            for (int c = 0; c < W; c++) {
-                const int pb = lane + 32 * c;
-                if ((m >> pb) & 1ull) {
-                    const int b = 2 * pb + sj;
-                    const int64_t p = pos + __popcll(m & below[c]);
-                    const uint32_t odd = cija ^ lij[c] ^ (uint32_t)(b < a);
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int cand = r + step;
+                    const uint32_t e = __shfl_sync(FULL, excl, cand & 31);
+                    if (cand < rows && e <= k) r = cand;
+                }
+                const uint64_t mr = __shfl_sync(FULL, m, r);
+                const uint32_t er = __shfl_sync(FULL, excl, r);
+                const int par_r = __shfl_sync(FULL, pa, r);
+                const uint32_t cr = __shfl_sync(FULL, cija_l, r);
+                if (k < total) {
+                    const int pb = select64(mr, (int)(k - er));
+                    const int a = 2 * par_r + si, b = 2 * pb + sj;
+                    const uint32_t odd = cr ^ (uint32_t)((parj >> pb) & 1ull) ^ (uint32_t)(i < b) ^
+                                         (uint32_t)(j < b) ^ (uint32_t)(b < a);
                     uint64_t t[W];
 #pragma unroll
-                    for (int w = 0; w < W; w++) t[w] = tija[w] ^ bmj[c][w];
-                    const double val = stg ? trow[pb] : __ldg(trow + pb);
-                    emit(t, flip_sign(val, odd), p);
+                    for (int w = 0; w < W; w++) t[w] = tij[w];
+                    flip_bit<W>(t, a);
+                    flip_bit<W>(t, b);
+                    const double val = stg ? slab[par_r * n + pb] : __ldg(slab + par_r * n + pb);
+                    emit(t, flip_sign(val, odd), pos + k);
                 }
             }
-            pos += __popcll(m);
+            pos += total;
+            // drop the rows just handled
+            if (rows >= __popcll(vs)) {
+                vs = 0;
+            } else {
+                const int last = select64(vs, rows - 1);
+                vs &= ~0ull << (last + 1);
+            }
         }
         if (stg) {
             __syncwarp();
