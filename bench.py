@@ -33,6 +33,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "coupled configs (+H_ij) generated & deduped per sec; % HBM roofline; energy+grad ms"
+
+# DRAM bytes per entry (dram__bytes_read.sum + dram__bytes_write.sum) of each
+# C-ABI call, from one ncu capture of the first 20k sources of the same
+# workload (profiles/traffic_mid_20k.md), scaled to a launch by its entries.
+# Set an entry to None when the kernels behind it change before a re-capture.
+TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 116.35, "cusci_gen_coupled (fill_kernel)": 15.94}
 UNIT = "entries/s"
 
 
@@ -248,6 +254,8 @@ def run_ours(args):
     gen_gbs = gen_bytes / (gen_ms * 1e-3) / 1e9
     dedup_gbs = dedup_bytes / (dedup_ms * 1e-3) / 1e9
     dominant = "cusci_dedup" if dedup_ms >= gen_ms else "cusci_gen_coupled (fill_kernel)"
+    tpe = TRAFFIC_B_PER_ENTRY.get(dominant)
+    traffic = None if tpe is None else tpe * total
     dom_gbs, dom_bytes, dom_ms = ((dedup_gbs, dedup_bytes, dedup_ms) if dedup_ms >= gen_ms
                                   else (gen_gbs, gen_bytes, gen_ms))
 
@@ -284,7 +292,7 @@ def run_ours(args):
                        "l2": "flushed between steps (256 MiB write outside the timed events); "
                              "each step also moves >40 GB"},
             "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": dom_gbs / hbm_peak, "traffic": None, "kernel": dominant,
+                         "frac": dom_gbs / hbm_peak, "traffic": traffic, "kernel": dominant,
                          "algorithmic_bytes_per_launch": dom_bytes, "ms_per_launch": dom_ms,
                          "peak_kind": f"{peak_kind} (copy, burst)"},
             "step_roofline": {"algorithmic_bytes": step_bytes,

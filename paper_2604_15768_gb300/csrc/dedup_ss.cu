@@ -498,13 +498,22 @@ struct LeafSmem {
 // digit at `shift`; pa / pb: optional 32-bit payload moved along (a, b, pa, pb
 // in shared or global memory)
 template <bool PAYLOAD>
-__device__ void leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, uint32_t *pb,
+__device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, uint32_t *pb,
                           int64_t n, int shift, LeafSmem &S) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < 256; d += T) S.hist[d] = 0;
+    if (threadIdx.x == 0) S.red_cnt[0] = 0;
     __syncthreads();
     for (int64_t k = threadIdx.x; k < n; k += T) atomicAdd(&S.hist[(a[k] >> shift) & 255], 1u);
     __syncthreads();
+    // a pass whose digit is the same for every key moves nothing: skip it
+    for (int d = threadIdx.x; d < 256; d += T)
+        if (S.hist[d] == (uint32_t)n) S.red_cnt[0] = 1;
+    __syncthreads();
+    if (S.red_cnt[0]) {
+        __syncthreads();
+        return false;
+    }
     if (wid == 0) {
         uint32_t c[8], s = 0;
 #pragma unroll
@@ -567,6 +576,7 @@ __device__ void leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, ui
         for (int d = threadIdx.x; d < 256; d += T) S.run[d] += S.ttot[d];
         __syncthreads();
     }
+    return true;
 }
 
 // walks the sorted keys a[0..n) (positions in the low pbits, or in pos[] when
@@ -657,8 +667,9 @@ __global__ void __launch_bounds__(T, 3)
                 a[k] = ((K2[ls + k] - r_lo) << pbits) | (uint64_t)k;
             __syncthreads();
             for (int shift = pbits; shift < pbits + rb; shift += 8) {
-                leaf_pass<false>(a, b, nullptr, nullptr, n, shift, S);
-                uint64_t *t = a; a = b; b = t;
+                if (leaf_pass<false>(a, b, nullptr, nullptr, n, shift, S)) {
+                    uint64_t *t = a; a = b; b = t;
+                }
             }
             leaf_walk(a, nullptr, n, pbits, r_lo, ls, U2, tmpU, ucnt + leaf, S);
         } else {
@@ -671,9 +682,10 @@ __global__ void __launch_bounds__(T, 3)
             }
             __syncthreads();
             for (int shift = 0; shift < rb; shift += 8) {
-                leaf_pass<true>(a, b, pa, pb, n, shift, S);
-                uint64_t *t = a; a = b; b = t;
-                uint32_t *tp = pa; pa = pb; pb = tp;
+                if (leaf_pass<true>(a, b, pa, pb, n, shift, S)) {
+                    uint64_t *t = a; a = b; b = t;
+                    uint32_t *tp = pa; pa = pb; pb = tp;
+                }
             }
             leaf_walk(a, pa, n, 0, r_lo, ls, U2, tmpU, ucnt + leaf, S);
         }

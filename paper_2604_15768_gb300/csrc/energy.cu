@@ -5,7 +5,9 @@
 // regenerated per row by the same warp enumeration as the fill pass and never
 // stored; membership j in S is resolved just in time (Stage 3, Sec. 4.3) in an
 // open-addressing hash table of S built in the caller's workspace (S is 1.6 MB
-// of keys for 200k determinants, so the table stays in L2).
+// of keys for 200k determinants, so the table stays in L2).  An exact
+// prefilter skips the probe for targets farther from S[0] -- per spin or in
+// total -- than every member of S.
 // Reductions are deterministic: per-row warp shuffles in a fixed pattern, then
 // one block that sums rows in a fixed order (Neumaier-compensated per thread)
 // followed by a fixed tree -- no floating-point atomics.
@@ -20,31 +22,40 @@ namespace {
 using namespace enumr;
 constexpr int EW = 8;  // warps per block
 
-__device__ __forceinline__ uint64_t mix64(uint64_t x) {
-    x ^= x >> 30;
-    x *= 0xbf58476d1ce4e5b9ull;
-    x ^= x >> 27;
-    x *= 0x94d049bb133111ebull;
-    x ^= x >> 31;
-    return x;
-}
-
+// multiplicative (Fibonacci) hash: top bits of the product select the slot
 template <int W>
-__device__ __forceinline__ uint64_t hash_det(const uint64_t *d) {
-    uint64_t h = mix64(d[0]);
-    if (W == 2) h = mix64(h ^ (d[W - 1] + 0x9e3779b97f4a7c15ull));
-    return h;
+__device__ __forceinline__ uint64_t hash_det(const uint64_t *d, int shift) {
+    uint64_t x = d[0];
+    if (W == 2) x ^= d[W - 1] * 0xc2b2ae3d27d4eb4full;
+    return (x * 0x9e3779b97f4a7c15ull) >> shift;
 }
 
 struct Table {
-    uint64_t *keys;  // [cap][W]
-    int64_t *vals;   // [cap], 0 = empty, else index + 1
-    uint64_t mask;   // cap - 1
+    uint64_t *keys;   // [cap][W]
+    int64_t *vals;    // [cap], 0 = empty, else index + 1
+    uint64_t mask;    // cap - 1
+    int shift;        // 64 - log2(cap)
+    const uint64_t *ref;       // S[0]
+    const uint32_t *maxdist;   // [3]: largest alpha, beta and total distance of S from S[0]
 };
+
+// occupation differences of t from the reference, per spin
+template <int W>
+__device__ __forceinline__ void spin_dist(const uint64_t *t, const uint64_t *ref, uint32_t &da,
+                                          uint32_t &db) {
+    da = 0;
+    db = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const uint64_t x = t[w] ^ ref[w];
+        da += __popcll(x & 0x5555555555555555ull);
+        db += __popcll(x & 0xAAAAAAAAAAAAAAAAull);
+    }
+}
 
 template <int W>
 __global__ void insert_S(Table tb, const uint64_t *__restrict__ S, int64_t nS,
-                         int32_t *__restrict__ status) {
+                         uint32_t *__restrict__ maxdist, int32_t *__restrict__ status) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nS;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint64_t d[W];
@@ -63,7 +74,12 @@ __global__ void insert_S(Table tb, const uint64_t *__restrict__ S, int64_t nS,
             }
             if (!gt) *status = CUSCI_ERR_INVALID;
         }
-        uint64_t h = hash_det<W>(d) & tb.mask;
+        uint32_t da, db;
+        spin_dist<W>(d, S, da, db);
+        atomicMax(maxdist, da);
+        atomicMax(maxdist + 1, db);
+        atomicMax(maxdist + 2, da + db);
+        uint64_t h = hash_det<W>(d, tb.shift);
         for (uint64_t probe = 0; probe <= tb.mask; probe++) {
             unsigned long long old =
                 atomicCAS((unsigned long long *)(tb.vals + h), 0ull, (unsigned long long)(i + 1));
@@ -79,7 +95,13 @@ __global__ void insert_S(Table tb, const uint64_t *__restrict__ S, int64_t nS,
 
 template <int W>
 __device__ __forceinline__ int64_t lookup(const Table &tb, const uint64_t (&t)[W]) {
-    uint64_t h = hash_det<W>(t) & tb.mask;
+    // exact prefilter: a target farther from S[0] (per spin) than every member
+    // of S cannot be in S
+    uint32_t da, db;
+    spin_dist<W>(t, tb.ref, da, db);
+    if (da > __ldg(tb.maxdist) || db > __ldg(tb.maxdist + 1) || da + db > __ldg(tb.maxdist + 2))
+        return -1;
+    uint64_t h = hash_det<W>(t, tb.shift);
     for (uint64_t probe = 0; probe <= tb.mask; probe++) {
         const int64_t v = __ldg(tb.vals + h);
         if (v == 0) return -1;
@@ -103,27 +125,18 @@ struct HpsiEmit {
     }
 };
 
-template <int W, bool STAGE>
+template <int W>
 __global__ void __launch_bounds__(32 * EW)
     hpsi_kernel(SysView v, Table tb, const uint64_t *__restrict__ S, int64_t nS, double eps,
-                const double *__restrict__ psi, double *__restrict__ hpsi,
-                int32_t *__restrict__ status) {
-    extern __shared__ __align__(16) unsigned char smem[];
+                const double *__restrict__ psi, double *__restrict__ hpsi) {
     const int lane = threadIdx.x & 31;
-    WarpStage st;
-    WarpStage *stp = nullptr;
-    if (STAGE) {
-        stage_init(st, smem + (threadIdx.x >> 5) * stage_bytes(v.slab, v.mrow), v.slab, v.mrow,
-                   lane, status);
-        stp = &st;
-    }
     const int64_t warp = (int64_t)blockIdx.x * EW + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * EW;
     for (int64_t i = warp; i < nS; i += nwarps) {
         Src<W> s;
         decode<W>(S + i * W, v.norb, s);
         HpsiEmit<W> em{&tb, psi, 0.0};
-        visit_source<W>(v, s, eps, lane, em, stp);
+        visit_source<W>(v, s, eps, lane, em);
         double a = em.acc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a = __dadd_rn(a, __shfl_xor_sync(FULL, a, o));
@@ -194,16 +207,20 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct EPlan {
     uint64_t cap;
-    size_t off_keys, off_vals, off_hp, bytes;
+    int log2cap;
+    size_t off_keys, off_vals, off_hp, off_md, bytes;
 };
 
 EPlan eplan(int64_t nS, int W) {
     EPlan p;
     p.cap = table_cap(nS);
+    p.log2cap = 0;
+    while ((1ull << p.log2cap) < p.cap) p.log2cap++;
     size_t off = 0;
     p.off_keys = off; off = align256(off + p.cap * 8 * W);
     p.off_vals = off; off = align256(off + p.cap * 8);
     p.off_hp = off; off = align256(off + (size_t)(nS > 0 ? nS : 1) * 8);
+    p.off_md = off; off = align256(off + 16);
     p.bytes = off;
     return p;
 }
@@ -216,8 +233,11 @@ cusci_status compute_hpsi(const cusci_system *sys, const uint64_t *d_S, int64_t 
         return fail(CUSCI_ERR_OOM, "energy: workspace %zu < %zu bytes", ws_bytes, p.bytes);
     if ((uintptr_t)d_ws & 255u) return fail(CUSCI_ERR_INVALID, "energy: workspace not 256-aligned");
     unsigned char *ws = (unsigned char *)d_ws;
-    Table tb{(uint64_t *)(ws + p.off_keys), (int64_t *)(ws + p.off_vals), p.cap - 1};
+    uint32_t *md = (uint32_t *)(ws + p.off_md);
+    Table tb{(uint64_t *)(ws + p.off_keys), (int64_t *)(ws + p.off_vals), p.cap - 1,
+             64 - p.log2cap, d_S, md};
     cudaError_t e = cudaMemsetAsync(tb.vals, 0, p.cap * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(md, 0, 16, st);
     if (e != cudaSuccess) return cuda_fail(e, "energy: table clear");
     const uint64_t *mask = NULL;
     cusci_status rc = masks_for(const_cast<cusci_system *>(sys), eps, st, &mask);
@@ -227,30 +247,14 @@ cusci_status compute_hpsi(const cusci_system *sys, const uint64_t *d_S, int64_t 
     if (ib > sm_count() * 8) ib = sm_count() * 8;
     int64_t want = (nS + EW - 1) / EW;
     int grid = (int)(want < sm_count() * 8 ? want : sm_count() * 8);
-    const size_t smem = (size_t)EW * stage_bytes(v.slab, v.mrow);
-    if (sys->W == 1 && smem <= 200 * 1024) {
-        insert_S<1><<<ib, 256, 0, st>>>(tb, d_S, nS, d_status);
-        static size_t attr = 0;
-        if (attr < smem) {
-            cudaError_t e2 = cudaFuncSetAttribute(hpsi_kernel<1, true>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)smem);
-            if (e2 != cudaSuccess) return cuda_fail(e2, "energy: shared-memory attribute");
-            attr = smem;
-        }
-        int per_sm = 0;
-        cudaError_t e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hpsi_kernel<1, true>,
-                                                                       32 * EW, smem);
-        if (e3 != cudaSuccess || per_sm < 1) per_sm = 1;
-        int g1 = (int)(want < sm_count() * per_sm ? want : sm_count() * per_sm);
-        if (g1 < 1) g1 = 1;
-        hpsi_kernel<1, true><<<g1, 32 * EW, smem, st>>>(v, tb, d_S, nS, eps, d_psi, hp, d_status);
-    } else if (sys->W == 1) {
-        insert_S<1><<<ib, 256, 0, st>>>(tb, d_S, nS, d_status);
-        hpsi_kernel<1, false><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp, d_status);
+    // unstaged: the hash probes are latency-bound, so full occupancy (64 warps
+    // per SM) beats shared-memory staging of the integral slabs here
+    if (sys->W == 1) {
+        insert_S<1><<<ib, 256, 0, st>>>(tb, d_S, nS, md, d_status);
+        hpsi_kernel<1><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp);
     } else {
-        insert_S<2><<<ib, 256, 0, st>>>(tb, d_S, nS, d_status);
-        hpsi_kernel<2, false><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp, d_status);
+        insert_S<2><<<ib, 256, 0, st>>>(tb, d_S, nS, md, d_status);
+        hpsi_kernel<2><<<grid, 32 * EW, 0, st>>>(v, tb, d_S, nS, eps, d_psi, hp);
     }
     CUSCI_LAUNCHED(2, "energy: H psi");
     return CUSCI_OK;
