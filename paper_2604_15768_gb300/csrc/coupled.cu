@@ -20,6 +20,8 @@
 // All FP64 arithmetic uses explicit round-to-nearest intrinsics (no contraction),
 // so elements are bit-identical to the closed forms summed in canonical order.
 
+#include <stdlib.h>
+
 #include "enumerate.cuh"
 
 namespace cusci {
@@ -116,13 +118,28 @@ int grid_for(int64_t n, int per_sm = 8) {
     return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
 }
 
+// Whether the fill stages each occupied pair's integral slab in shared memory
+// by bulk copies (W = 1 only).  Off by default: on GB300 the unstaged form,
+// whose slab reads hit L1/L2 at four times the occupancy (64 instead of 16
+// warps per SM), measured 13.4 ms against 16.6 ms on the 100k-source mid
+// workload.  CUSCI_FILL_STAGE=1 in the environment selects the staged form
+// (identical results).
+bool fill_stage_default() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("CUSCI_FILL_STAGE");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
+
 // fill launch: staged integral slabs in shared memory when they fit
 template <int W>
 cusci_status launch_fill(const SysView &v, const uint64_t *d_dets, int64_t n, double eps,
                          const int64_t *d_offsets, uint64_t *d_out_dets, double *d_out_h,
                          int32_t *d_status, cudaStream_t st) {
     const size_t smem = (size_t)WARPS_PER_BLOCK * stage_bytes(v.slab, v.mrow);
-    if (W == 1 && smem <= 200 * 1024) {
+    if (W == 1 && smem <= 200 * 1024 && fill_stage_default()) {
         static size_t attr = 0;
         if (attr < smem) {
             cudaError_t e = cudaFuncSetAttribute(fill_kernel<W, true>,

@@ -213,7 +213,7 @@ static Plan make_plan(int64_t total, int W, int n_bits, int n_ones) {
         p.key_bits = bitlen128(space - 1);
     } else {
         p.mode = 0;
-        p.KW = W;
+        p.KW = n_bits <= 64 ? 1 : W;  // high words of narrow keys are zero
         p.key_bits = n_bits;
     }
     if (p.key_bits < 1) p.key_bits = 1;

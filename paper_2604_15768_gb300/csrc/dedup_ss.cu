@@ -25,7 +25,8 @@
 //     reverse index is gathered back through the two stored slot arrays --
 //     reads with the same L2 locality as the scatters, instead of a random
 //     4-byte scatter per entry into the reverse index.
-// Single-word keys are compared as they are; two-word keys by their rank in the
+// Keys of at most 64 significant bits are compared as their low word (a second
+// word must then be zero); wider two-word keys by their rank in the
 // combinatorial number system (order preserving for a fixed number of
 // electrons) when it fits 42 bits; other inputs take the LSD path in dedup.cu.
 // A leaf whose packed form would not fit 64 bits, or that exceeds the
@@ -93,7 +94,7 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool eligible(int64_t N, int W, int n_bits, int n_ones, int *mode, int *key_bits) {
     if (N < ((int64_t)1 << 22) || N >= ((int64_t)1 << 32)) return false;
-    if (W == 1 && n_bits <= MAX_RAW_BITS) { *mode = 0; *key_bits = n_bits; return true; }
+    if (n_bits <= MAX_RAW_BITS) { *mode = 0; *key_bits = n_bits; return true; }
     if (n_ones >= 0 && n_ones < 64 && n_bits * (n_ones + 1) <= BT_MAX) {
         const unsigned __int128 space = binom128(n_bits, n_ones);
         const int kb = space > 1 ? bitlen128(space - 1) : 1;
@@ -164,17 +165,21 @@ __device__ __forceinline__ void stage(uint64_t *dst, const uint64_t *__restrict_
 }
 
 // sort key of one W-word key: combinatorial rank (mode 1) or raw word (mode 0);
-// *ones receives the number of set bits among the low n_bits.
+// *ones receives the number of set bits among the low n_bits, or -1 if a bit
+// at or above n_bits is set.
 template <int W>
 __device__ __forceinline__ uint64_t sort_key(const uint64_t *__restrict__ k, int mode, int n_bits,
                                              int kcols, const uint64_t *bt, int *ones) {
     uint64_t r = 0;
     int c = 0;
+    bool above = false;
 #pragma unroll
     for (int w = 0; w < W; w++) {
         uint64_t x = __ldg(k + w);
         const int hi = n_bits - 64 * w;
-        if (hi < 64) x &= hi <= 0 ? 0ull : ((1ull << hi) - 1);
+        const uint64_t keep = hi >= 64 ? ~0ull : (hi <= 0 ? 0ull : ((1ull << hi) - 1));
+        if (x & ~keep) above = true;
+        x &= keep;
         if (mode == 0) {
             if (w == 0) r = x;
             c += __popcll(x);
@@ -186,7 +191,7 @@ __device__ __forceinline__ uint64_t sort_key(const uint64_t *__restrict__ k, int
             if (c < kcols) r += bt[pos * kcols + c];
         }
     }
-    *ones = c;
+    *ones = above ? -1 : c;  // -1: bits above n_bits (invalid key)
     return r;
 }
 
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(T)
         for (int u = 0; u < U1; u++) {
             const int64_t i = i0 + (int64_t)u * T;
             if (i < end) {
-                if (n_ones >= 0 && ones[u] != n_ones) bad = true;
+                if ((n_ones >= 0 && ones[u] != n_ones) || ones[u] < 0) bad = true;
                 const int b = count_less(S1, log2B1, x[u]);
                 bid1[i] = (uint16_t)b;
                 atomicAdd(&h[b], 1u);
@@ -708,8 +713,12 @@ __global__ void __launch_bounds__(T)
     for (int64_t leaf = warp; leaf < NL; leaf += nw) {
         const int64_t ls = leaf_start[leaf], c = ucnt[leaf], ub = ubase[leaf];
         for (int64_t k = lane; k < c; k += 32) {
-            if (mode == 0) unique[ub + k] = tmpU[ls + k];
-            else unrank_to<W>(tmpU[ls + k], mode, n_bits, n_ones, kcols, bt, unique + (ub + k) * W);
+            if (mode == 0) {
+                unique[(ub + k) * W] = tmpU[ls + k];
+                if (W == 2) unique[(ub + k) * W + 1] = 0;
+            } else {
+                unrank_to<W>(tmpU[ls + k], mode, n_bits, n_ones, kcols, bt, unique + (ub + k) * W);
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *n_unique = ubase[NL];

@@ -96,21 +96,42 @@ __global__ void __launch_bounds__(HT)
     }
 }
 
+// block-aggregated compaction of the occupied slots (one atomic per block)
 template <int W>
-__global__ void hash_compact(const uint64_t *__restrict__ tab, uint64_t cap,
-                             uint64_t *__restrict__ out, unsigned long long *__restrict__ cursor,
-                             int64_t out_cap, int32_t *__restrict__ status) {
-    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < cap;
-         k += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t x0 = tab[k * W];
-        if (x0 == EMPTY) continue;
-        const unsigned long long at = atomicAdd(cursor, 1ull);
-        if ((int64_t)at >= out_cap) {
-            if (status) *status = CUSCI_ERR_OVERFLOW;
-            continue;
+__global__ void __launch_bounds__(HT)
+    hash_compact(const uint64_t *__restrict__ tab, uint64_t cap, uint64_t *__restrict__ out,
+                 unsigned long long *__restrict__ cursor, int64_t out_cap,
+                 int32_t *__restrict__ status) {
+    __shared__ uint32_t wcount[HT / 32];
+    __shared__ unsigned long long base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t stride = (uint64_t)gridDim.x * HT;
+    for (uint64_t k0 = blockIdx.x * (uint64_t)HT; k0 < cap; k0 += stride) {
+        const uint64_t k = k0 + threadIdx.x;
+        const bool full = k < cap && tab[k * W] != EMPTY;
+        const unsigned bal = __ballot_sync(0xffffffffu, full);
+        if (lane == 0) wcount[wid] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t s = 0;
+            for (int w = 0; w < HT / 32; w++) {
+                const uint32_t c = wcount[w];
+                wcount[w] = s;
+                s += c;
+            }
+            base = s ? atomicAdd(cursor, (unsigned long long)s) : 0ull;
         }
+        __syncthreads();
+        if (full) {
+            const unsigned long long at = base + wcount[wid] + __popc(bal & ((1u << lane) - 1u));
+            if ((int64_t)at < out_cap) {
 #pragma unroll
-        for (int w = 0; w < W; w++) out[at * W + w] = tab[k * W + w];
+                for (int w = 0; w < W; w++) out[at * W + w] = tab[k * W + w];
+            } else if (status) {
+                *status = CUSCI_ERR_OVERFLOW;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -317,12 +338,12 @@ extern "C" cusci_status cusci_stream_gen_dedup(
     void *dws = q; q += al(ws);
     const size_t peak2 = (size_t)(q - (unsigned char *)d_pool);
     if (peak2 > pool_bytes) return fail(CUSCI_ERR_OOM, "stream: pool too small for the final sort");
-    int cb = (int)((slots + 255) / 256);
+    int cb = (int)((slots + HT - 1) / HT);
     if (cb > sm_count() * 8) cb = sm_count() * 8;
     if (W == 1)
-        hash_compact<1><<<cb, 256, 0, st>>>(tab, slots, raw, d_ctr + 1, unique_capacity, d_status);
+        hash_compact<1><<<cb, HT, 0, st>>>(tab, slots, raw, d_ctr + 1, unique_capacity, d_status);
     else
-        hash_compact<2><<<cb, 256, 0, st>>>(tab, slots, raw, d_ctr + 1, unique_capacity, d_status);
+        hash_compact<2><<<cb, HT, 0, st>>>(tab, slots, raw, d_ctr + 1, unique_capacity, d_status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "stream: compaction");
     note_launches(1);

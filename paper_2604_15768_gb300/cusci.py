@@ -280,26 +280,41 @@ def stream_pool_bytes(sys: System, n_sources: int, batch_entries: int,
     return b.value
 
 
+def stream_buffers(sys: System, dets: np.ndarray, batch_entries: int, unique_capacity: int,
+                   host_capacity: int = 0):
+    """Caller-side buffers of ``stream_gen_dedup``: pinned host sources, the
+    device pool, pinned host sinks (if host_capacity > 0) and the distinct set."""
+    dets = np.ascontiguousarray(dets, dtype=np.uint64).reshape(-1, sys.W)
+    need = stream_pool_bytes(sys, dets.shape[0], batch_entries, unique_capacity)
+    buf = {"src": torch.from_numpy(dets.view(np.int64)).pin_memory(),
+           "pool": torch.empty(need, dtype=torch.uint8, device="cuda"),
+           "unique": torch.empty((unique_capacity, sys.W), dtype=torch.int64, device="cuda"),
+           "hd": None, "hh": None}
+    if host_capacity > 0:
+        buf["hd"] = torch.empty((host_capacity, sys.W), dtype=torch.int64).pin_memory()
+        buf["hh"] = torch.empty(host_capacity, dtype=torch.float64).pin_memory()
+    return buf
+
+
 def stream_gen_dedup(sys: System, dets: np.ndarray, eps: float, batch_entries: int,
                      unique_capacity: int, host_capacity: int | None = None, offload=True,
-                     pool=None, stream=None):
+                     pool=None, stream=None, buffers=None):
     """Mini-batched generation + de-duplication (host sources in, host coupled
     lists and device distinct set out).  Returns (offsets, host_dets, host_h,
-    unique, stats) with host arrays pinned."""
+    unique, stats) with host arrays pinned.  ``buffers`` (from stream_buffers)
+    are reused when given."""
     dets = np.ascontiguousarray(dets, dtype=np.uint64).reshape(-1, sys.W)
     n = dets.shape[0]
-    h_src = torch.from_numpy(dets.view(np.int64)).pin_memory()
-    need = stream_pool_bytes(sys, n, batch_entries, unique_capacity)
-    if pool is None or pool.numel() < need:
-        pool = torch.empty(need, dtype=torch.uint8, device="cuda")
+    if buffers is None:
+        buffers = stream_buffers(sys, dets, batch_entries, unique_capacity,
+                                 int(host_capacity) if offload else 0)
+        if pool is not None and pool.numel() >= buffers["pool"].numel():
+            buffers["pool"] = pool
+    h_src, pool, uniq = buffers["src"], buffers["pool"], buffers["unique"]
     offsets = np.zeros(n + 1, dtype=np.int64)
-    hd = hh = None
-    cap = 0
-    if offload:
-        cap = int(host_capacity)
-        hd = torch.empty((max(cap, 1), sys.W), dtype=torch.int64).pin_memory()
-        hh = torch.empty(max(cap, 1), dtype=torch.float64).pin_memory()
-    uniq = torch.empty((unique_capacity, sys.W), dtype=torch.int64, device="cuda")
+    hd = buffers["hd"] if offload else None
+    hh = buffers["hh"] if offload else None
+    cap = 0 if hd is None else hd.shape[0]
     nu = ctypes.c_int64(0)
     stats = np.zeros(4, dtype=np.int64)
     _check(load().cusci_stream_gen_dedup(
@@ -443,7 +458,6 @@ class Batch:
         self.out_h = torch.empty(max(self.total, 1), dtype=torch.float64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         ws = 1
-        self.dd = []
         for k, s in enumerate(self.systems):
             m = int(self.entry_begin[k + 1] - self.entry_begin[k])
             ws = max(ws, dedup_workspace(max(m, 1), 2, s.M, s.n_alpha + s.n_beta))
@@ -461,6 +475,7 @@ class Batch:
             a, b = int(self.entry_begin[k]), int(self.entry_begin[k + 1])
             if b == a:
                 continue
+            # two-word keys; for one-word systems (M <= 64) the library sorts word 0 only
             dedup_into(self.out_d[a:b], s.M, s.n_alpha + s.n_beta, self.unique[a:b],
                        self.inverse[a:b], self.n_unique[k:k + 1], self.dd_ws, stream=stream)
 

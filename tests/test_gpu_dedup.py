@@ -146,3 +146,24 @@ def test_full_size_dedup_properties():
     used = torch.zeros(nu, dtype=torch.bool, device="cuda")
     used[inv.long()] = True
     assert bool(used.all())
+
+
+@pytest.mark.parametrize("n", [100_000, 5_000_000])
+def test_two_word_keys_with_zero_high_word(n):
+    """Keys stored as two words whose significant bits fit the low word are sorted
+    as one-word keys (both the LSD and the sample-sort paths)."""
+    rng = np.random.default_rng(n)
+    base = rng.integers(0, 1 << 40, size=max(1, n // 5)).astype(np.uint64)
+    keys = np.zeros((n, 2), dtype=np.uint64)
+    keys[:, 0] = base[rng.integers(0, base.size, size=n)]
+    compare(keys, 40, -1)
+
+
+def test_bits_above_declared_width_are_reported():
+    rng = np.random.default_rng(3)
+    keys = rng.integers(0, 1 << 40, size=(5_000_000, 1)).astype(np.uint64)
+    keys[123, 0] |= np.uint64(1) << np.uint64(45)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cusci.dedup(to_dev(keys), 40, -1, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 1
