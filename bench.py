@@ -109,6 +109,20 @@ class ClockSampler:
         return out
 
 
+def aggregate_over_ranks(ms_local: float, entries_local: int, device=None):
+    """Whole-job figures of independent replicas: the slowest rank's time and the
+    sum of all ranks' entries (plain values when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, entries_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    e = torch.tensor([entries_local], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(e.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -237,12 +251,10 @@ def run_ours(args):
         t_dedup.append(m[2].elapsed_time(m[3]))
     step_ms = [a + b + c for a, b, c in zip(t_count, t_gen, t_dedup)]
     ms = float(np.mean(step_ms))
+    ms, job_entries = aggregate_over_ranks(ms, total, device=dev)
     if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
-    value = ws * total / (ms * 1e-3)
+    value = job_entries / (ms * 1e-3)
 
     # algorithmic bytes (8W+8 written per entry by the fill, 8W read + inverse
     # written per entry and 8W per distinct key by the dedup, 8W + 16 per source)
@@ -423,15 +435,13 @@ def run_stream(args, dev):
     total = int(cusci.count_coupled(sysd, d, s.eps).sum().item())
     del d
     hcap = total
-    pool = torch.empty(cusci.stream_pool_bytes(sysd, s.dets.shape[0], batch, ucap),
-                       dtype=torch.uint8, device=dev)
+    buffers = cusci.stream_buffers(sysd, s.dets, batch, ucap, hcap)
     res = None
     times = []
-    for it in range(2):
+    for it in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = cusci.stream_gen_dedup(sysd, s.dets, s.eps, batch, ucap, host_capacity=hcap,
-                                     pool=pool)
+        res = cusci.stream_gen_dedup(sysd, s.dets, s.eps, batch, ucap, buffers=buffers)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     off, hd, hh, uniq, st = res

@@ -116,7 +116,7 @@ Plan make_plan(int64_t N, int W, int n_bits, int n_ones, int mode, int key_bits)
     p.NL = (int64_t)p.B1 * B2;
     p.NS = p.NL * OVS;
     if (p.NS > N) p.NS = N;
-    p.G = sm_count() * 2;
+    p.G = sm_count() * 3;
     p.per_cta = ((N + p.G - 1) / p.G + 31) / 32 * 32;
     // sample sort grid (radix building blocks)
     const int64_t tiles = (p.NS + radix::RTILE - 1) / radix::RTILE;
@@ -272,7 +272,7 @@ __global__ void make_splitters(const uint64_t *__restrict__ sorted, int64_t NS, 
     }
 }
 
-constexpr int U1 = 4;   // keys per thread in flight in the partition passes
+constexpr int U1 = 8;   // keys per thread in flight in the partition passes
 constexpr int UG = 8;   // gathers in flight per thread in the reverse-index passes
 
 template <int W>
@@ -544,11 +544,14 @@ __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, ui
             const int64_t k = t0 + wid * (LRI * 32) + r * 32 + lane;
             v[r] = k < n ? a[k] : 0;
         }
+        const int64_t wbase = t0 + wid * (LRI * 32);
 #pragma unroll
         for (int r = 0; r < LRI; r++) {
-            const int64_t k = t0 + wid * (LRI * 32) + r * 32 + lane;
+            const int64_t k = wbase + r * 32 + lane;
             const bool valid = k < n;
             dg[r] = valid ? (uint32_t)((v[r] >> shift) & 255) : 256u;
+            rk[r] = 0;
+            if (wbase + r * 32 >= n) continue;  // whole round past the end (warp-uniform)
             const unsigned peers = __match_any_sync(FULL, dg[r]);
             const int below = __popc(peers & ((1u << lane) - 1u));
             uint32_t prev = valid ? S.wcnt[wid][dg[r]] : 0;
