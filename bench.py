@@ -38,7 +38,7 @@ METRIC = "coupled configs (+H_ij) generated & deduped per sec; % HBM roofline; e
 # C-ABI call, from one ncu capture of the first 20k sources of the same
 # workload (profiles/traffic_mid_20k.md), scaled to a launch by its entries.
 # Set an entry to None when the kernels behind it change before a re-capture.
-TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 116.35, "cusci_gen_coupled (fill_kernel)": 15.94}
+TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 116.42, "cusci_gen_coupled (fill_kernel)": 15.93}
 UNIT = "entries/s"
 
 

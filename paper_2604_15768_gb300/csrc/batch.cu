@@ -54,6 +54,10 @@ struct BatchFill {
 template <int W>
 struct FillAdapter {
     BatchFill &f;
+    __device__ __forceinline__ bool pair_possible(const uint64_t (&)[W], int, int) const {
+        return true;
+    }
+    __device__ __forceinline__ bool row_possible(const uint64_t (&)[W], int) const { return true; }
     __device__ __forceinline__ void operator()(const uint64_t (&t)[W], double h, int64_t rank) {
         f.template operator()<W>(t, h, rank);
     }

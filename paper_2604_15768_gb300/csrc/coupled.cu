@@ -35,6 +35,10 @@ struct FillEmit {
     uint64_t *__restrict__ out_d;
     double *__restrict__ out_h;
     int64_t beg, end;
+    __device__ __forceinline__ bool pair_possible(const uint64_t (&)[W], int, int) const {
+        return true;
+    }
+    __device__ __forceinline__ bool row_possible(const uint64_t (&)[W], int) const { return true; }
     __device__ __forceinline__ void operator()(const uint64_t (&t)[W], double h, int64_t rank) {
         const int64_t p = beg + rank;
         if (p < end) {

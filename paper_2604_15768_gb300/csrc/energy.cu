@@ -119,6 +119,23 @@ struct HpsiEmit {
     const Table *tb;
     const double *__restrict__ psi;
     double acc;
+    // every target of the pair / row toggles `flips` more bits (a, b), each of
+    // which can shorten its distance to S[0] by at most one: if even then it is
+    // farther than every member of S, none of them is in S
+    __device__ __forceinline__ bool within(const uint64_t (&t)[W], int fa, int fb) const {
+        uint32_t da, db;
+        spin_dist<W>(t, tb->ref, da, db);
+        const uint32_t ma = __ldg(tb->maxdist), mb = __ldg(tb->maxdist + 1),
+                       mt = __ldg(tb->maxdist + 2);
+        return (int)da - fa <= (int)ma && (int)db - fb <= (int)mb &&
+               (int)(da + db) - fa - fb <= (int)mt;
+    }
+    __device__ __forceinline__ bool pair_possible(const uint64_t (&t)[W], int si, int sj) const {
+        return within(t, (si == 0) + (sj == 0), (si == 1) + (sj == 1));
+    }
+    __device__ __forceinline__ bool row_possible(const uint64_t (&t)[W], int sj) const {
+        return within(t, sj == 0, sj == 1);
+    }
     __device__ __forceinline__ void operator()(const uint64_t (&t)[W], double h, int64_t) {
         const int64_t j = lookup<W>(*tb, t);
         if (j >= 0) acc = __dadd_rn(acc, __dmul_rn(h, __ldg(psi + j)));

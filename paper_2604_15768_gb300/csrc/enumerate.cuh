@@ -329,7 +329,10 @@ __device__ __forceinline__ size_t pair_index(int n, int i, int j) {
 // Visits every kept entry of the coupled set of source s in canonical order.
 // emit(t, h, rank) is called by the lane that owns the entry: t is the target
 // determinant, h the signed FP64 element, rank its position in the source's
-// list (0 = diagonal).  The call is warp-collective (all 32 lanes, uniform
+// list (0 = diagonal).  emit.pair_possible(tij, si, sj) / emit.row_possible(
+// tija, sj) may rule out every double of an occupied pair (tij: source with i
+// and j removed) or of a row (tija: also a added); emitters that need exact
+// positions must return true.  The call is warp-collective (all 32 lanes, uniform
 // control flow); returns |C_s|.
 template <int W, class Emit>
 __device__ __forceinline__ int64_t visit_source(const SysView &v, const Src<W> &s, double eps,
@@ -411,7 +414,11 @@ __device__ __forceinline__ int64_t visit_source(const SysView &v, const Src<W> &
         flip_bit<W>(tij, j);
         const uint64_t virj = sel2(s.vir, sj);
         const uint64_t parj = sel2(s.par, sj);
-        for (uint64_t vs = sel2(s.vir, si); vs;) {
+        // an emitter may rule out a whole pair (all its targets lie outside the
+        // set it looks targets up in); positions then stop counting that pair,
+        // which only emitters that ignore positions may do
+        const bool pair_live = emit.pair_possible(tij, si, sj);
+        for (uint64_t vs = pair_live ? sel2(s.vir, si) : 0ull; vs;) {
             // row of this lane: the lane-th remaining virtual a
             const int rows = __popcll(vs) < 32 ? __popcll(vs) : 32;
             int pa = -1;
@@ -419,6 +426,13 @@ __device__ __forceinline__ int64_t visit_source(const SysView &v, const Src<W> &
             if (lane < rows) {
                 pa = select64(vs, lane);
                 m = (stg ? mrow[pa] : __ldg(mrow + pa)) & virj;
+                if (m) {
+                    uint64_t tija[W];
+#pragma unroll
+                    for (int w = 0; w < W; w++) tija[w] = tij[w];
+                    flip_bit<W>(tija, 2 * pa + si);
+                    if (!emit.row_possible(tija, sj)) m = 0;
+                }
             }
             const uint32_t cnt = (uint32_t)__popcll(m);
             uint32_t incl = cnt;
