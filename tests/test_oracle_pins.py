@@ -214,3 +214,14 @@ def test_screening_is_strict_and_keeps_diagonal():
         assert (np.abs(hv[off[i] + 1:off[i + 1]]) > 0.05).all()
     huge = osys.count(s.dets, 1e300)
     assert (huge == 1).all()
+
+
+def test_tiny_spectrum_golden():
+    """The oracle's coupled lists reproduce the stored brute-force spectrum."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tiny_spectrum.txt")
+    ref = np.array([float(x) for x in open(path) if not x.startswith("#")])
+    s = synth.config_system("tiny")
+    off, td, hv = O.OracleSystem.of(s).gen(s.dets, -1.0)
+    H = _dense_from_lists(s.dets, off, td, hv)
+    assert np.abs(np.linalg.eigvalsh(H)[:5] - ref).max() < 1e-10
