@@ -58,6 +58,8 @@ constexpr int LTILE = T * LRI;    // 2048
 constexpr int MAX_KEY_BITS = 42;   // rank keys: packed with up to 22 position bits
 constexpr int MAX_RAW_BITS = 64;   // raw single-word keys
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int LG_CELLS1 = 13;      // level-1 lookup table: 8192 cells over the sampled key range
+constexpr int LG_CELLS2 = 10;      // level-2 lookup table per bucket: 1024 cells
 
 struct Plan {
     int64_t N;
@@ -71,7 +73,7 @@ struct Plan {
     int s_passes;
     size_t o_bt, o_samp, o_samp2, o_sidx, o_sidx2, o_shist, o_sbase, o_scanws, o_LS, o_H1,
         o_base1, o_bid1, o_K1, o_dest1, o_bid2, o_K2, o_dest2, o_U2, o_tmpU, o_leafst, o_ucnt,
-        o_ubase, o_pay, o_kbase, bytes;
+        o_ubase, o_pay, o_kbase, o_T1, o_krange, bytes;
 };
 
 unsigned __int128 binom128(int m, int k) {
@@ -155,6 +157,8 @@ Plan make_plan(int64_t N, int W, int n_bits, int n_ones, int mode, int key_bits)
     p.o_ubase = o; o = al(o + (p.NL + 1) * 8);
     p.o_pay = o; o = al(o + N * 8);
     p.o_kbase = o; o = al(o + ((size_t)p.B1 + 1) * 8);
+    p.o_T1 = o; o = al(o + ((size_t)(1 << LG_CELLS1) + 1) * 2);
+    p.o_krange = o; o = al(o + 16);
     p.bytes = o;
     return p;
 }
@@ -224,6 +228,37 @@ __device__ __forceinline__ int count_less(const uint64_t *S, int lg, uint64_t x)
     return b;
 }
 
+// number of entries of S that are < x, knowing it lies in [lo, hi]
+__device__ __forceinline__ int count_less_in(const uint64_t *S, int lo, int hi, uint64_t x) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (S[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// cell of x in a table of 2^lg cells of width 2^shift starting at kmin
+__device__ __forceinline__ int cell_of(uint64_t x, uint64_t kmin, int shift, int lg) {
+    if (x <= kmin) return 0;
+    const uint64_t c = (x - kmin) >> shift;
+    return c >= (uint64_t)((1 << lg) - 1) ? (1 << lg) - 1 : (int)c;
+}
+
+// table T[c] = number of splitters S[0..n) below the start of cell c, T[2^lg] = n - 1
+__device__ __forceinline__ void build_cells(const uint64_t *S, int lgS, int n, uint64_t kmin,
+                                            int shift, int lg, uint16_t *T) {
+    for (int c = threadIdx.x; c <= (1 << lg); c += blockDim.x) {
+        if (c == (1 << lg)) {
+            T[c] = (uint16_t)(n - 1);
+        } else {
+            const uint64_t off = (uint64_t)c << shift;
+            const uint64_t start = (off > ~0ull - kmin) ? ~0ull : kmin + off;
+            T[c] = (uint16_t)count_less(S, lgS, start);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ kernels
 __global__ void build_bt(uint64_t *bt, int n_bits, int kcols) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -256,6 +291,24 @@ __global__ void __launch_bounds__(T)
     }
 }
 
+// level-1 lookup table over the sampled key range [sorted[0], sorted[NS-1]]
+__global__ void build_T1(const uint64_t *__restrict__ sorted, int64_t NS,
+                         const uint64_t *__restrict__ LS, int B1, int log2B1,
+                         uint16_t *__restrict__ T1, uint64_t *__restrict__ krange) {
+    __shared__ uint64_t S1[MAX_B1];
+    for (int b = threadIdx.x; b < B1; b += blockDim.x) S1[b] = LS[(int64_t)b * B2 + B2 - 1];
+    __syncthreads();
+    const uint64_t kmin = sorted[0], kmax = sorted[NS - 1];
+    const uint64_t span = kmax - kmin;
+    const int bits = span == 0 ? 0 : 64 - __clzll((long long)span);
+    const int shift = bits > LG_CELLS1 ? bits - LG_CELLS1 : 0;
+    if (threadIdx.x == 0) {
+        krange[0] = kmin;
+        krange[1] = (uint64_t)shift;
+    }
+    build_cells(S1, log2B1, B1, kmin, shift, LG_CELLS1, T1);
+}
+
 __global__ void make_splitters(const uint64_t *__restrict__ sorted, int64_t NS, int64_t NL,
                                uint64_t *__restrict__ LS) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < NL;
@@ -279,17 +332,22 @@ template <int W>
 __global__ void __launch_bounds__(T)
     hist1(const uint64_t *__restrict__ keys, int64_t N, int64_t per_cta, int mode, int n_bits,
           int n_ones, int kcols, const uint64_t *__restrict__ bt_g,
-          const uint64_t *__restrict__ LS, int B1, int log2B1, uint16_t *__restrict__ bid1,
+          const uint64_t *__restrict__ LS, int B1, int log2B1, const uint16_t *__restrict__ T1,
+          const uint64_t *__restrict__ krange, uint16_t *__restrict__ bid1,
           uint32_t *__restrict__ H1, int32_t *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char sm[];
     uint64_t *S1 = (uint64_t *)sm;
     uint64_t *bt = S1 + B1;
-    uint32_t *h = (uint32_t *)(bt + BT_MAX);
+    uint32_t *h = (uint32_t *)(bt + (mode == 1 ? BT_MAX : 0));
+    uint16_t *T1s = (uint16_t *)(h + B1);
     for (int b = threadIdx.x; b < B1; b += T) {
         S1[b] = LS[(int64_t)b * B2 + B2 - 1];
         h[b] = 0;
     }
+    for (int c = threadIdx.x; c <= (1 << LG_CELLS1); c += T) T1s[c] = T1[c];
     if (mode == 1) stage(bt, bt_g, n_bits * kcols);
+    const uint64_t kmin = krange[0];
+    const int kshift = (int)krange[1];
     __syncthreads();
     const int64_t beg = (int64_t)blockIdx.x * per_cta;
     int64_t end = beg + per_cta;
@@ -310,7 +368,8 @@ __global__ void __launch_bounds__(T)
             const int64_t i = i0 + (int64_t)u * T;
             if (i < end) {
                 if ((n_ones >= 0 && ones[u] != n_ones) || ones[u] < 0) bad = true;
-                const int b = count_less(S1, log2B1, x[u]);
+                const int c = cell_of(x[u], kmin, kshift, LG_CELLS1);
+                const int b = count_less_in(S1, T1s[c], T1s[c + 1], x[u]);
                 bid1[i] = (uint16_t)b;
                 atomicAdd(&h[b], 1u);
             }
@@ -406,6 +465,7 @@ __global__ void __launch_bounds__(T)
     __shared__ uint64_t L[B2];
     __shared__ uint32_t h[B2];
     __shared__ unsigned long long run[B2];
+    __shared__ uint16_t T2[(1 << LG_CELLS2) + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int b1 = blockIdx.x;
     const int64_t kb = kbase[b1];
@@ -413,6 +473,14 @@ __global__ void __launch_bounds__(T)
         L[t] = LS[(int64_t)b1 * B2 + t];
         h[t] = 0;
     }
+    // this bucket's keys lie in (S1[b1-1], S1[b1]]: a lookup table over that range
+    const uint64_t blo = b1 == 0 ? 0ull : LS[(int64_t)b1 * B2 - 1] + 1;
+    const uint64_t bhi = LS[(int64_t)b1 * B2 + B2 - 1];
+    const uint64_t bspan = bhi > blo ? bhi - blo : 0ull;
+    const int bbits = bspan == 0 ? 0 : 64 - __clzll((long long)bspan);
+    const int bshift = bbits > LG_CELLS2 ? bbits - LG_CELLS2 : 0;
+    __syncthreads();
+    build_cells(L, LOG2_B2, B2, blo, bshift, LG_CELLS2, T2);
     __syncthreads();
     for (int c = wid; c < G; c += WARPS) {
         const int64_t sb = base1[(int64_t)c * B1 + b1];
@@ -428,7 +496,8 @@ __global__ void __launch_bounds__(T)
             for (int u = 0; u < U1; u++) {
                 const int64_t k = k0 + u * 32 + lane;
                 if (k < len) {
-                    const int b = count_less(L, LOG2_B2, x[u]);
+                    const int c = cell_of(x[u], blo, bshift, LG_CELLS2);
+                    const int b = count_less_in(L, T2[c], T2[c + 1], x[u]);
                     bid2[sb + k] = (uint8_t)b;
                     atomicAdd(&h[b], 1u);
                 }
@@ -846,14 +915,20 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
     }
     make_splitters<<<(int)((p.NL + 255) / 256), 256, 0, st>>>((const uint64_t *)samp, p.NS, p.NL,
                                                                LS);
+    uint16_t *T1 = (uint16_t *)(ws + p.o_T1);
+    uint64_t *krange = (uint64_t *)(ws + p.o_krange);
+    build_T1<<<1, 1024, 0, st>>>((const uint64_t *)samp, p.NS, LS, p.B1, p.log2B1, T1, krange);
+    launches++;
     launches++;
     // level 1
-    const size_t sm_h1 = (size_t)p.B1 * 8 + BT_MAX * 8 + (size_t)p.B1 * 4;
+    const size_t sm_h1 = (size_t)p.B1 * 8 + (p.mode == 1 ? BT_MAX * 8 : 0) + (size_t)p.B1 * 4 +
+                         ((size_t)(1 << LG_CELLS1) + 1) * 2;
     const size_t sm_x1 = (size_t)p.B1 * 8 + BT_MAX * 8;
     {
         static bool attr = false;
         if (!attr) {
-            cusci_status rc = set_smem((const void *)hist1<W>, (size_t)MAX_B1 * 12 + BT_MAX * 8);
+            cusci_status rc = set_smem((const void *)hist1<W>, (size_t)MAX_B1 * 12 + BT_MAX * 8 +
+                                                   ((size_t)(1 << LG_CELLS1) + 1) * 2);
             if (rc == CUSCI_OK) rc = set_smem((const void *)scatter1<W>, (size_t)MAX_B1 * 8 + BT_MAX * 8);
             if (rc == CUSCI_OK) rc = set_smem((const void *)leaf_sort, sizeof(LeafSmem));
             if (rc != CUSCI_OK) return rc;
@@ -861,7 +936,7 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
         }
     }
     hist1<W><<<p.G, T, sm_h1, st>>>(keys, p.N, p.per_cta, p.mode, p.n_bits, p.n_ones, p.kcols, bt,
-                                    LS, p.B1, p.log2B1, bid1, H1, status);
+                                    LS, p.B1, p.log2B1, T1, krange, bid1, H1, status);
     const int64_t nh1 = (int64_t)p.B1 * p.G;
     widen_u32<<<sms * 2, 256, 0, st>>>(H1, nh1, base1);
     cusci_status rc = exclusive_scan_i64(base1, nh1, base1, scanws, st);
