@@ -561,6 +561,7 @@ struct LeafSmem {
     uint64_t A[LEAF_CAP];
     uint64_t B[LEAF_CAP];
     uint32_t hist[256];
+    uint32_t hnext[256];  // histogram of the next pass's digit, built while scattering
     uint32_t run[256];
     uint32_t ttot[256];
     uint16_t wcnt[WARPS][256];
@@ -572,19 +573,34 @@ struct LeafSmem {
 // digit at `shift`; pa / pb: optional 32-bit payload moved along (a, b, pa, pb
 // in shared or global memory)
 template <bool PAYLOAD>
+__device__ void leaf_hist(const uint64_t *a, int64_t n, int shift, uint32_t *hist) {
+    for (int d = threadIdx.x; d < 256; d += T) hist[d] = 0;
+    __syncthreads();
+    for (int64_t k = threadIdx.x; k < n; k += T) atomicAdd(&hist[(a[k] >> shift) & 255], 1u);
+    __syncthreads();
+}
+
+// One pass of a stable LSD radix sort of a[0..n) into b[0..n) on the 8-bit
+// digit at `shift`; pa / pb: optional 32-bit payload moved along (a, b, pa, pb
+// in shared or global memory).  S.hist must hold this digit's histogram; when
+// next_shift >= 0 the histogram of the digit at next_shift is built into
+// S.hnext while scattering.  Returns false (and moves nothing) when every key
+// has the same digit.
+template <bool PAYLOAD>
 __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, uint32_t *pb,
-                          int64_t n, int shift, LeafSmem &S) {
+                          int64_t n, int shift, int next_shift, LeafSmem &S) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < 256; d += T) S.hist[d] = 0;
     if (threadIdx.x == 0) S.red_cnt[0] = 0;
+    for (int d = threadIdx.x; d < 256; d += T) S.hnext[d] = 0;
     __syncthreads();
-    for (int64_t k = threadIdx.x; k < n; k += T) atomicAdd(&S.hist[(a[k] >> shift) & 255], 1u);
-    __syncthreads();
-    // a pass whose digit is the same for every key moves nothing: skip it
     for (int d = threadIdx.x; d < 256; d += T)
         if (S.hist[d] == (uint32_t)n) S.red_cnt[0] = 1;
     __syncthreads();
     if (S.red_cnt[0]) {
+        // nothing moves; the next digit's histogram still has to be built
+        if (next_shift >= 0)
+            for (int64_t k = threadIdx.x; k < n; k += T)
+                atomicAdd(&S.hnext[(a[k] >> next_shift) & 255], 1u);
         __syncthreads();
         return false;
     }
@@ -647,6 +663,7 @@ __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, ui
                 const uint32_t dst = S.run[dg[r]] + S.wcnt[wid][dg[r]] + rk[r];
                 b[dst] = v[r];
                 if (PAYLOAD) pb[dst] = pa[t0 + wid * (LRI * 32) + r * 32 + lane];
+                if (next_shift >= 0) atomicAdd(&S.hnext[(v[r] >> next_shift) & 255], 1u);
             }
         }
         __syncthreads();
@@ -654,6 +671,25 @@ __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, ui
         __syncthreads();
     }
     return true;
+}
+
+// runs the LSD passes over bits [lo, hi) of a[0..n) (ping-ponging with b);
+// returns the buffer holding the sorted keys
+template <bool PAYLOAD>
+__device__ uint64_t *leaf_sort_bits(uint64_t *a, uint64_t *b, uint32_t *&pa, uint32_t *&pb,
+                                    int64_t n, int lo, int hi, LeafSmem &S) {
+    if (lo >= hi) return a;
+    leaf_hist<PAYLOAD>(a, n, lo, S.hist);
+    for (int shift = lo; shift < hi; shift += 8) {
+        const int next = shift + 8 < hi ? shift + 8 : -1;
+        if (leaf_pass<PAYLOAD>(a, b, pa, pb, n, shift, next, S)) {
+            uint64_t *t = a; a = b; b = t;
+            if (PAYLOAD) { uint32_t *tp = pa; pa = pb; pb = tp; }
+        }
+        for (int d = threadIdx.x; d < 256; d += T) S.hist[d] = S.hnext[d];
+        __syncthreads();
+    }
+    return a;
 }
 
 // walks the sorted keys a[0..n) (positions in the low pbits, or in pos[] when
@@ -743,11 +779,8 @@ __global__ void __launch_bounds__(T, 3)
             for (int64_t k = threadIdx.x; k < n; k += T)
                 a[k] = ((K2[ls + k] - r_lo) << pbits) | (uint64_t)k;
             __syncthreads();
-            for (int shift = pbits; shift < pbits + rb; shift += 8) {
-                if (leaf_pass<false>(a, b, nullptr, nullptr, n, shift, S)) {
-                    uint64_t *t = a; a = b; b = t;
-                }
-            }
+            uint32_t *np = nullptr, *nq = nullptr;
+            a = leaf_sort_bits<false>(a, b, np, nq, n, pbits, pbits + rb, S);
             leaf_walk(a, nullptr, n, pbits, r_lo, ls, U2, tmpU, ucnt + leaf, S);
         } else {
             // global memory: keys (key - min) with positions in a separate array
@@ -758,12 +791,7 @@ __global__ void __launch_bounds__(T, 3)
                 pa[k] = (uint32_t)k;
             }
             __syncthreads();
-            for (int shift = 0; shift < rb; shift += 8) {
-                if (leaf_pass<true>(a, b, pa, pb, n, shift, S)) {
-                    uint64_t *t = a; a = b; b = t;
-                    uint32_t *tp = pa; pa = pb; pb = tp;
-                }
-            }
+            a = leaf_sort_bits<true>(a, b, pa, pb, n, 0, rb, S);
             leaf_walk(a, pa, n, 0, r_lo, ls, U2, tmpU, ucnt + leaf, S);
         }
     }
