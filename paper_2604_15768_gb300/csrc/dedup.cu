@@ -36,11 +36,13 @@ namespace {
 
 using namespace radix;
 
-__device__ uint64_t g_binom[128 * BINOM_K];
+__device__ uint64_t g_binom[128 * BINOM_K];    // C(m, k), saturated at 2^64 - 1
+__device__ ulonglong2 g_binom2[128 * BINOM_K];  // C(m, k) exact in 128 bits (lo, hi)
 bool g_binom_ready[64] = {false};
 
 // ------------------------------------------------------------------ key transform
-// mode 0: raw low n_bits bits; mode 1: colex rank (KW must be 1)
+// mode 0: raw low n_bits bits; mode 1: combinatorial rank in 64 bits (KW 1);
+// mode 2: combinatorial rank in 128 bits (KW 2)
 template <int W, int KW>
 __global__ void prepare_keys(const uint64_t *__restrict__ keys, int64_t total, int n_bits,
                              int n_ones, int mode, Key<KW> *__restrict__ out,
@@ -60,7 +62,25 @@ __global__ void prepare_keys(const uint64_t *__restrict__ keys, int64_t total, i
             ones += __popcll(x[w]);
         }
         Key<KW> r;
-        if (mode == 1) {
+        if (mode == 2) {
+            // rank in 128 bits (KW == 2): keys whose rank space exceeds 2^64
+            if (ones != n_ones) bad = true;
+            uint64_t lo = 0, hi = 0;
+            int c = 0;
+#pragma unroll
+            for (int w = 0; w < W; w++)
+                for (uint64_t b = x[w]; b; b &= b - 1) {
+                    int pos = 64 * w + __ffsll((long long)b) - 1;
+                    c++;
+                    if (c < BINOM_K) {
+                        const ulonglong2 v = g_binom2[pos * BINOM_K + c];
+                        lo += v.x;
+                        hi += v.y + (lo < v.x ? 1ull : 0ull);
+                    }
+                }
+            r.w[0] = lo;
+            r.w[KW - 1] = hi;
+        } else if (mode == 1) {
             if (ones != n_ones) bad = true;
             uint64_t rank = 0;
             int c = 0;
@@ -107,40 +127,15 @@ __global__ void __launch_bounds__(UT)
     }
 }
 
-template <int KW, int W>
-__device__ __forceinline__ void unrank_store(const Key<KW> &k, int mode, int n_bits, int n_ones,
-                                             uint64_t *__restrict__ out) {
-    uint64_t x[W];
-#pragma unroll
-    for (int w = 0; w < W; w++) x[w] = 0;
-    if (mode == 1) {
-        uint64_t r = k.w[0];
-        int c = n_bits - 1;
-        for (int t = n_ones; t >= 1; t--) {
-            // largest c with C(c, t) <= r
-            while (c >= t && g_binom[c * BINOM_K + t] > r) c--;
-            if (c < t - 1) c = t - 1;  // remaining positions are forced (C(c,t)=0)
-            if (c >= 0) {
-                uint64_t v = (c >= t) ? g_binom[c * BINOM_K + t] : 0;
-                r -= v;
-                x[c >> 6] |= 1ull << (c & 63);
-            }
-            c--;
-        }
-    } else {
-#pragma unroll
-        for (int w = 0; w < W; w++) x[w] = w < KW ? k.w[w] : 0;
-    }
-#pragma unroll
-    for (int w = 0; w < W; w++) out[w] = x[w];
-}
-
+// the distinct keys are copied from the input through the index payload (no
+// un-ranking)
 template <int KW, int W>
 __global__ void __launch_bounds__(UT)
     unique_scatter(const Key<KW> *__restrict__ keys, const uint32_t *__restrict__ idx,
-                   int64_t total, const int64_t *__restrict__ tile_off, int mode, int n_bits,
-                   int n_ones, uint64_t *__restrict__ unique, void *__restrict__ inverse,
-                   int index_bytes, int64_t *__restrict__ n_unique) {
+                   int64_t total, const int64_t *__restrict__ tile_off, int n_bits,
+                   const uint64_t *__restrict__ orig, uint64_t *__restrict__ unique,
+                   void *__restrict__ inverse, int index_bytes,
+                   int64_t *__restrict__ n_unique) {
     __shared__ uint32_t warp_tot[UT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * UTILE;
@@ -168,10 +163,18 @@ __global__ void __launch_bounds__(UT)
         int64_t k = base + threadIdx.x * UI + r;
         if (k >= total) break;
         uid += head[r];
-        const uint32_t orig = idx[k];
-        if (index_bytes == 4) reinterpret_cast<int32_t *>(inverse)[orig] = (int32_t)uid;
-        else reinterpret_cast<int64_t *>(inverse)[orig] = uid;
-        if (head[r]) unrank_store<KW, W>(keys[k], mode, n_bits, n_ones, unique + uid * W);
+        const uint32_t oi = idx[k];
+        if (index_bytes == 4) reinterpret_cast<int32_t *>(inverse)[oi] = (int32_t)uid;
+        else reinterpret_cast<int64_t *>(inverse)[oi] = uid;
+        if (head[r]) {
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                uint64_t x = orig[(int64_t)oi * W + w];
+                const int hi = n_bits - 64 * w;
+                x &= hi >= 64 ? ~0ull : (hi <= 0 ? 0ull : ((1ull << hi) - 1));
+                unique[uid * W + w] = x;
+            }
+        }
         if (k == total - 1) *n_unique = uid + 1;
     }
 }
@@ -207,9 +210,15 @@ static Plan make_plan(int64_t total, int W, int n_bits, int n_ones) {
     memset(&p, 0, sizeof(p));
     const unsigned __int128 space = n_ones >= 0 ? binom128(n_bits, n_ones) : 0;
     const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+    const unsigned __int128 sat = (unsigned __int128)1 << 100;
     if (n_ones >= 0 && n_ones < BINOM_K && space >= 1 && space <= two64) {
         p.mode = 1;
         p.KW = 1;
+        p.key_bits = bitlen128(space - 1);
+    } else if (W == 2 && n_ones >= 0 && n_ones < BINOM_K && space > two64 && space < sat &&
+               bitlen128(space - 1) < n_bits) {
+        p.mode = 2;
+        p.KW = 2;
         p.key_bits = bitlen128(space - 1);
     } else {
         p.mode = 0;
@@ -255,12 +264,20 @@ cusci_status ensure_binom() {
     cudaGetDevice(&dev);
     if (dev < 64 && g_binom_ready[dev]) return CUSCI_OK;
     static uint64_t host[128 * BINOM_K];
+    static ulonglong2 host2[128 * BINOM_K];
+    static unsigned __int128 pas[128][BINOM_K];
     for (int m = 0; m < 128; m++)
         for (int k = 0; k < BINOM_K; k++) {
-            unsigned __int128 v = binom128(m, k);
+            unsigned __int128 v;
+            if (k == 0) v = 1;
+            else if (m == 0) v = 0;
+            else v = pas[m - 1][k - 1] + pas[m - 1][k];  // at most C(127, 63) < 2^124
+            pas[m][k] = v;
             host[m * BINOM_K + k] = v > (unsigned __int128)(~0ull) ? ~0ull : (uint64_t)v;
+            host2[m * BINOM_K + k] = make_ulonglong2((uint64_t)v, (uint64_t)(v >> 64));
         }
     cudaError_t e = cudaMemcpyToSymbol(g_binom, host, sizeof(host));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_binom2, host2, sizeof(host2));
     if (e != cudaSuccess) return cuda_fail(e, "dedup: binomial table upload");
     if (dev < 64) g_binom_ready[dev] = true;
     return CUSCI_OK;
@@ -307,8 +324,8 @@ cusci_status run_dedup(const Plan &p, const uint64_t *d_keys, int64_t total, int
     head_counts<KW><<<(unsigned)ut, UT, 0, st>>>(k0, total, tiles);
     cusci_status rc = exclusive_scan_i64(tiles, ut, tileoff, scanws, st);
     if (rc != CUSCI_OK) return rc;
-    unique_scatter<KW, W><<<(unsigned)ut, UT, 0, st>>>(k0, i0, total, tileoff, p.mode, n_bits,
-                                                       n_ones, d_unique, d_inverse, index_bytes,
+    unique_scatter<KW, W><<<(unsigned)ut, UT, 0, st>>>(k0, i0, total, tileoff, n_bits, d_keys,
+                                                       d_unique, d_inverse, index_bytes,
                                                        d_n_unique);
     CUSCI_LAUNCHED(2, "dedup unique");
     return CUSCI_OK;
