@@ -8,30 +8,32 @@
 //     bucket; the skewed key distribution (configurations near the reference
 //     determinant are far more frequent) is balanced by the sample, not by the
 //     key bits.
-//  2. Partition in two levels instead of the all-to-all exchange (Step 3): a
-//     4096-way split by the level-1 splitters, then a 128-way split of every
-//     level-1 bucket, giving ~524k leaf buckets of ~3k entries.  Each
-//     partition pass is a contiguous-chunk scatter whose per-block write
-//     fronts (4096 buckets x 304 blocks x 32 B = 40 MB) stay inside the
-//     129 MB L2, so DRAM sees whole sectors.  Slots inside a bucket are handed
-//     out with warp-aggregated shared-memory atomics; the slot of every entry
-//     is kept (4 B) so the reverse index can be gathered back later.
+//  2. Partition in two levels instead of the all-to-all exchange (Step 3): up
+//     to a 4096-way split by the level-1 splitters, then a 256-way split of
+//     every level-1 bucket, giving leaf buckets of ~1.6k entries (about 1M of
+//     them for 1.7e9 keys).  Splitter searches are bracketed by lookup tables
+//     over the key range (the sample's range for level 1, the bucket's range
+//     for level 2).  The level-1 output is laid out block-major: each block
+//     writes its chunk's entries into per-bucket runs inside its own contiguous
+//     region, so its write fronts and the later gathers stay inside a few TLB
+//     pages and L2 lines.  Slots inside a run are handed out with
+//     warp-aggregated shared-memory atomics; the slot of every entry is kept
+//     (4 B) so the reverse index can be gathered back later.
 //  3. Each leaf is loaded into shared memory, packed as
 //     (key - leaf_min) << pos_bits | position, LSD radix-sorted there (stable
-//     8-bit passes over the key bits only), and walked once to mark run heads:
-//     the local unique id of every position and the distinct keys.
+//     8-bit passes over the key bits only; a pass whose digit is constant is
+//     skipped; the next digit's histogram is built while scattering), and
+//     walked once to mark run heads: the local unique id of every position and
+//     the distinct keys.  Leaves that do not fit are sorted in global memory
+//     with their positions in a separate array.
 //  4. A scan of per-leaf distinct counts gives the global unique ids; the
-//     distinct keys are compacted (un-ranked back to determinants), and the
-//     reverse index is gathered back through the two stored slot arrays --
-//     reads with the same L2 locality as the scatters, instead of a random
-//     4-byte scatter per entry into the reverse index.
+//     distinct keys are compacted, and the reverse index is gathered back
+//     through the two stored slot arrays -- reads with the same locality as
+//     the scatters, instead of a random 4-byte scatter per entry.
 // Keys of at most 64 significant bits are compared as their low word (a second
 // word must then be zero); wider two-word keys by their rank in the
 // combinatorial number system (order preserving for a fixed number of
 // electrons) when it fits 42 bits; other inputs take the LSD path in dedup.cu.
-// A leaf whose packed form would not fit 64 bits, or that exceeds the
-// shared-memory capacity, is sorted in global memory with its positions in a
-// separate array.
 
 #include <string.h>
 
