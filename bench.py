@@ -38,6 +38,15 @@ METRIC = "coupled configs (+H_ij) generated & deduped per sec; % HBM roofline; e
 # C-ABI call, from one ncu capture of the first 20k sources of the same
 # workload (profiles/traffic_mid_20k.md), scaled to a launch by its entries.
 # Set an entry to None when the kernels behind it change before a re-capture.
+WORKLOADS = {
+    "mid": "mid: 52 spin orbitals, 7a+7b electrons, {n} sources (random excitations of "
+           "rank<=4), eps=1e-8",
+    "tiny": "tiny: 16 spin orbitals, 4a+4b electrons, all {n} determinants of the FCI space, "
+            "eps=0",
+    "large": "large: 120 spin orbitals (2 words), 10a+10b electrons, {n} sources, eps=1e-6, "
+             "in HBM (no streaming)",
+}
+
 TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 116.42, "cusci_gen_coupled (fill_kernel)": 15.93}
 UNIT = "entries/s"
 
@@ -138,7 +147,7 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     from paper_2604_15768_gb300 import synth
-    s = synth.config_system("mid", n_dets=args.ref_sources)
+    s = synth.config_system(args.workload, n_dets=ref_sample(args))
     osys = O.OracleSystem.of(s)
     times, entries = [], 0
     for it in range(args.warmup + args.steps):
@@ -157,11 +166,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "mid: 52 spin orbitals, 7a+7b, eps 1e-8, first "
-                               f"{args.ref_sources} of the 100k sources (bounded CPU sample)",
-                   "sources": args.ref_sources, "entries_per_step": entries},
+        "config": {"workload": WORKLOADS[args.workload].format(n=s.dets.shape[0])
+                   + " (bounded CPU sample: the first sources of the workload)",
+                   "sources": int(s.dets.shape[0]), "entries_per_step": entries},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
-                         "sample": f"first {args.ref_sources} sources of the 100k-source mid "
+                         "sample": f"first {s.dets.shape[0]} sources of the {args.workload} "
                                    "workload, count+gen+dedup"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -185,7 +194,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     hbm_peak, peak_kind = _peaks()
 
-    s = synth.config_system("mid", n_dets=args.sources)
+    s = synth.config_system(args.workload, n_dets=args.sources)
     sysd = cusci.System.of(s)
     n, W = s.dets.shape
     n_bits, n_ones = 2 * s.norb, s.n_alpha + s.n_beta
@@ -266,7 +275,7 @@ def run_ours(args):
     gen_gbs = gen_bytes / (gen_ms * 1e-3) / 1e9
     dedup_gbs = dedup_bytes / (dedup_ms * 1e-3) / 1e9
     dominant = "cusci_dedup" if dedup_ms >= gen_ms else "cusci_gen_coupled (fill_kernel)"
-    tpe = TRAFFIC_B_PER_ENTRY.get(dominant)
+    tpe = TRAFFIC_B_PER_ENTRY.get(dominant) if args.workload == "mid" else None
     traffic = None if tpe is None else tpe * total
     dom_gbs, dom_bytes, dom_ms = ((dedup_gbs, dedup_bytes, dedup_ms) if dedup_ms >= gen_ms
                                   else (gen_gbs, gen_bytes, gen_ms))
@@ -297,8 +306,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
             "data": "synthetic",
-            "config": {"workload": "mid: 52 spin orbitals, 7a+7b electrons, "
-                                   f"{n} sources (random excitations of rank<=4), eps=1e-8",
+            "config": {"workload": WORKLOADS[args.workload].format(n=n),
                        "sources": n, "entries_per_step": total, "unique_per_step": n_unique,
                        "inverse_bytes": idx_bytes, "parallelism": f"replicas{ws}",
                        "l2": "flushed between steps (256 MiB write outside the timed events); "
@@ -489,10 +497,18 @@ def run_batched(args, dev):
                         "of count+scan+fill+per-system dedup"}
 
 
+REF_SOURCES = {"mid": 2000, "tiny": None, "large": 60}
+
+
+def ref_sample(args):
+    n = args.ref_sources if args.ref_sources is not None else REF_SOURCES[args.workload]
+    return n
+
+
 def run_cpu_baseline(args):
     from oracle import oracle as O
     from paper_2604_15768_gb300 import synth
-    s = synth.config_system("mid", n_dets=args.ref_sources)
+    s = synth.config_system(args.workload, n_dets=ref_sample(args))
     osys = O.OracleSystem.of(s)
     t0 = time.perf_counter()
     counts = osys.count(s.dets, s.eps)
@@ -500,8 +516,8 @@ def run_cpu_baseline(args):
     O.dedup(td)
     t = time.perf_counter() - t0
     return {"value": int(off[-1]) / t, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
-            "sample": f"first {args.ref_sources} sources of the mid workload (count+gen+dedup, "
-                      f"{int(off[-1])} entries, {t:.1f} s)"}
+            "sample": f"first {s.dets.shape[0]} sources of the {args.workload} workload "
+                      f"(count+gen+dedup, {int(off[-1])} entries, {t:.1f} s)"}
 
 
 def main(argv=None):
@@ -510,9 +526,13 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--sources", type=int, default=100_000)
+    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS),
+                    help="workload of the timed step (the metric is quoted on 'mid')")
+    ap.add_argument("--sources", type=int, default=None,
+                    help="number of sources (default: the workload's own)")
     ap.add_argument("--energy-sources", type=int, default=200_000)
-    ap.add_argument("--ref-sources", type=int, default=2000)
+    ap.add_argument("--ref-sources", type=int, default=None,
+                    help="sources of the CPU-oracle sample (default per workload)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-energy", dest="energy", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
