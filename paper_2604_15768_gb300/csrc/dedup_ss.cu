@@ -97,7 +97,7 @@ int bitlen128(unsigned __int128 x) {
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool eligible(int64_t N, int W, int n_bits, int n_ones, int *mode, int *key_bits) {
-    if (N < ((int64_t)1 << 20) || N >= ((int64_t)1 << 32)) return false;
+    if (N < ((int64_t)1 << 22) || N >= ((int64_t)1 << 32)) return false;
     if (n_bits <= MAX_RAW_BITS) { *mode = 0; *key_bits = n_bits; return true; }
     if (n_ones >= 0 && n_ones < 64 && n_bits * (n_ones + 1) <= BT_MAX) {
         const unsigned __int128 space = binom128(n_bits, n_ones);

@@ -96,7 +96,7 @@ def test_workspace_too_small_is_an_error():
         cusci._check(rc, "cusci_dedup")
 
 
-# ---- sample-sort path (taken for >= 2^20 keys whose sort key fits one word or a 42-bit rank)
+# ---- sample-sort path (taken for >= 2^22 keys whose sort key fits one word or a 42-bit rank)
 
 def test_sample_sort_rank_keys_vs_oracle():
     s, td = coupled_keys("mid", 400)          # ~6.7M entries, ranks of 41 bits
