@@ -454,7 +454,12 @@ def run_stream(args, dev):
         times.append(time.perf_counter() - t0)
     off, hd, hh, uniq, st = res
     t = min(times[1:]) if len(times) > 1 else times[0]
+    hbm_peak, _ = _peaks()
+    # W = 2: 16 + 8 written per entry, 16 read + 4 inverse-equivalent + 16 per distinct key
+    alg = st["total"] * 48 + int(uniq.shape[0]) * 16
     return {"entries_per_s": st["total"] / t, "ms": t * 1e3, "entries": st["total"],
+            "algorithmic_bytes": alg, "achieved_gbs": alg / t / 1e9,
+            "frac_of_hbm": alg / t / 1e9 / hbm_peak,
             "unique": int(uniq.shape[0]), "batches": st["batches"],
             "batch_entries": batch, "pool_bytes": st["pool_bytes"],
             "pool_peak_bytes": st["pool_peak"], "batch_region_bytes": 2 * batch * 24,
@@ -489,7 +494,16 @@ def run_batched(args, dev):
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(z))
     ms = float(np.median(ts))
+    hbm_peak, _ = _peaks()
+    nus = b.n_unique.cpu().numpy()
+    alg = 0
+    for k, x in enumerate(systems):
+        m = int(b.entry_begin[k + 1] - b.entry_begin[k])
+        wbytes = 8 * x.W
+        alg += m * (wbytes + 8) + m * (wbytes + 4) + int(nus[k]) * wbytes
     return {"entries_per_s": b.total / (ms * 1e-3), "ms": ms, "entries": b.total,
+            "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
+            "frac_of_hbm": alg / (ms * 1e-3) / 1e9 / hbm_peak,
             "systems": len(systems), "sources": int(b.n), "chunk": int(chunk),
             "unique_total": int(b.n_unique.sum().item()), "synth_s": t_synth,
             "workload": f"64 systems, norb 10..50, 4..16 electrons, sources "
