@@ -187,6 +187,34 @@ cusci_status cusci_energy_bwd(const cusci_system *sys, const uint64_t *d_S, int6
                               const double *d_grad_out, double *d_grad, void *d_ws,
                               size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------ local energy
+ * The SCI energy in the paper's local form (Eq. 5; Stage 3 of Sec. 3): over the
+ * coupled lists of the sources (CSR d_offsets[n+1], elements d_h) and the
+ * reverse index d_inverse into the distinct coupled set U (both as written by
+ * cusci_gen_coupled and cusci_dedup), with amplitudes d_psi_u on U:
+ *   y_i = sum_{e in row i} H_e psi_u[inverse[e]],  psi_i = psi_u[inverse[offsets[i]]]
+ *   E = sum_i psi_i y_i / sum_i psi_i^2.
+ * Every row must start with its diagonal (the source itself) and every inverse
+ * value must lie in [0, n_unique).  d_y: device double[n], nullable.  d_E,
+ * d_norm2: device double[1].  The forward reduction is deterministic.
+ * Workspace: cusci_local_energy_workspace bytes, 256-byte aligned. */
+cusci_status cusci_local_energy_workspace(int64_t n, size_t *bytes);
+cusci_status cusci_local_energy_fwd(const int64_t *d_offsets, int64_t n, const double *d_h,
+                                    const void *d_inverse, int index_bytes,
+                                    const double *d_psi_u, double *d_y, double *d_E,
+                                    double *d_norm2, void *d_ws, size_t ws_bytes, void *stream);
+/* Adjoint: d_grad_u[u] = g ( sum_{e: inverse[e]=u} psi_{i(e)} H_e
+ *   + sum_{rows i whose source is u} (y_i - 2 E psi_i) ) / norm2, g = *d_grad_out
+ * (NULL: 1).  d_y from the forward call, or NULL to recompute (then the
+ * workspace is needed).  The scatter-add uses FP64 atomics: results agree with
+ * any other summation order to rounding, not bit for bit. */
+cusci_status cusci_local_energy_bwd(const int64_t *d_offsets, int64_t n, const double *d_h,
+                                    const void *d_inverse, int index_bytes,
+                                    const double *d_psi_u, int64_t n_unique, const double *d_y,
+                                    const double *d_E, const double *d_norm2,
+                                    const double *d_grad_out, double *d_grad_u, void *d_ws,
+                                    size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------ streaming
  * Generation + de-duplication in mini-batches out of a caller-owned device
  * pool (Sec. 4.3: mini-batch execution, compute/transfer overlap, Stage 1

@@ -62,6 +62,8 @@ def _lib():
             lib.orc_apply_op.restype = I
             lib.orc_apply_op.argtypes = [P, I, I]
             lib.orc_threads.restype = I
+            lib.orc_local_energy.restype = None
+            lib.orc_local_energy.argtypes = [P, I64, P, P, P, I64, D, P, P, P, P]
             lib.fci_brute_H.restype = I64
             lib.fci_brute_H.argtypes = [I, P, P, D, P, I64, I, P]
             lib.fci_brute_column.restype = I64
@@ -134,6 +136,23 @@ class OracleSystem:
         _lib().orc_energy_grad(_p(psi), _p(hp), psi.size, float(E[0]), float(n2[0]), float(g),
                                _p(grad))
         return float(E[0]), float(n2[0]), hp, grad
+
+
+def local_energy(offsets, h, inverse, psi_u, g=1.0):
+    """(E, norm2, y, grad_u) of the local-energy form over CSR coupled lists whose
+    targets index the distinct set through ``inverse``."""
+    offsets = _c(offsets, np.int64)
+    h = _c(h, np.float64)
+    inverse = _c(inverse, np.int64)
+    psi_u = _c(psi_u, np.float64)
+    n = offsets.size - 1
+    y = np.zeros(n)
+    grad = np.zeros(psi_u.size)
+    E = np.zeros(1)
+    n2 = np.zeros(1)
+    _lib().orc_local_energy(_p(offsets), n, _p(h), _p(inverse), _p(psi_u), psi_u.size, float(g),
+                            _p(y), _p(E), _p(n2), _p(grad))
+    return float(E[0]), float(n2[0]), y, grad
 
 
 def dedup(keys, W=None):

@@ -322,3 +322,36 @@ int orc_threads(void) {
     return 1;
 #endif
 }
+
+/* ---------------- local energy (Eq. 5 form) ----------------
+ * Coupled lists of the sources S in CSR form (offsets[n+1], H per entry) and,
+ * per entry, the index of its target in the distinct set U (inverse); psi_u
+ * are the amplitudes on U.  The source i is its own first entry (the diagonal),
+ * so psi_i = psi_u[inverse[offsets[i]]].
+ *   y_i = sum_{e in row i} H_e psi_u[inverse[e]]   (entries in order)
+ *   E   = sum_i psi_i y_i / sum_i psi_i^2           (Neumaier, index order)
+ *   dE/dpsi_u[u] = ( sum_{e: inverse[e] = u} psi_{i(e)} H_e
+ *                    + sum_{i: s(i) = u} (y_i - 2 E psi_i) ) / sum psi_i^2
+ * (times the incoming gradient g). */
+void orc_local_energy(const int64_t *offsets, int64_t n, const double *h, const int64_t *inverse,
+                      const double *psi_u, int64_t n_unique, double g, double *y, double *E,
+                      double *norm2, double *grad_u) {
+    neumaier num = {0.0, 0.0}, den = {0.0, 0.0};
+    for (int64_t i = 0; i < n; i++) {
+        double acc = 0.0;
+        for (int64_t e = offsets[i]; e < offsets[i + 1]; e++) acc += h[e] * psi_u[inverse[e]];
+        y[i] = acc;
+        const double p = psi_u[inverse[offsets[i]]];
+        nm_add(&num, p * acc);
+        nm_add(&den, p * p);
+    }
+    *norm2 = nm_value(&den);
+    *E = nm_value(&num) / *norm2;
+    for (int64_t u = 0; u < n_unique; u++) grad_u[u] = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        const double p = psi_u[inverse[offsets[i]]];
+        for (int64_t e = offsets[i]; e < offsets[i + 1]; e++) grad_u[inverse[e]] += p * h[e];
+        grad_u[inverse[offsets[i]]] += y[i] - 2.0 * (*E) * p;
+    }
+    for (int64_t u = 0; u < n_unique; u++) grad_u[u] = g * (grad_u[u] / *norm2);
+}

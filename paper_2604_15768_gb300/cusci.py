@@ -64,6 +64,10 @@ _PROTOS = {
     "cusci_batch_sources": (_I64, [_P]),
     "cusci_batch_count": (_I, [_P, _P, _D, _P, _P]),
     "cusci_batch_gen": (_I, [_P, _P, _D, _P, _P, _P, _P, _P]),
+    "cusci_local_energy_workspace": (_I, [_I64, ctypes.POINTER(_SZ)]),
+    "cusci_local_energy_fwd": (_I, [_P, _I64, _P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "cusci_local_energy_bwd": (_I, [_P, _I64, _P, _P, _I, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ,
+                                    _P]),
     "cusci_energy_workspace": (_I, [_P, _I64, ctypes.POINTER(_SZ)]),
     "cusci_energy_fwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _SZ, _P, _P]),
     "cusci_energy_bwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -374,6 +378,62 @@ def energy_bwd(sys: System, S, psi, eps, E, norm2, hpsi=None, grad_out=None, wor
                                    _ptr(workspace), 0 if workspace is None else workspace.numel(),
                                    _stream(stream)), "cusci_energy_bwd")
     return grad
+
+
+def local_energy_workspace(n: int) -> int:
+    ws = ctypes.c_size_t()
+    _check(load().cusci_local_energy_workspace(int(n), ctypes.byref(ws)),
+           "cusci_local_energy_workspace")
+    return ws.value
+
+
+def local_energy_fwd(offsets, h, inverse, psi_u, workspace=None, save_y=True, stream=None):
+    """(E, norm2, y or None) of the local-energy form (Eq. 5) as device tensors."""
+    n = offsets.shape[0] - 1
+    ib = 4 if inverse.dtype == torch.int32 else 8
+    need = local_energy_workspace(n)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=h.device)
+    E = torch.empty(1, dtype=torch.float64, device=h.device)
+    n2 = torch.empty(1, dtype=torch.float64, device=h.device)
+    y = torch.empty(n, dtype=torch.float64, device=h.device) if save_y else None
+    _check(load().cusci_local_energy_fwd(_ptr(offsets), n, _ptr(h), _ptr(inverse), ib,
+                                         _ptr(psi_u), _ptr(y), _ptr(E), _ptr(n2),
+                                         _ptr(workspace), workspace.numel(), _stream(stream)),
+           "cusci_local_energy_fwd")
+    return E, n2, y
+
+
+def local_energy_bwd(offsets, h, inverse, psi_u, E, norm2, y=None, grad_out=None,
+                     workspace=None, stream=None):
+    n = offsets.shape[0] - 1
+    ib = 4 if inverse.dtype == torch.int32 else 8
+    if y is None and (workspace is None or workspace.numel() < local_energy_workspace(n)):
+        workspace = torch.empty(local_energy_workspace(n), dtype=torch.uint8, device=h.device)
+    grad = torch.empty_like(psi_u)
+    g = None if grad_out is None else grad_out.reshape(1).to(torch.float64).contiguous()
+    _check(load().cusci_local_energy_bwd(_ptr(offsets), n, _ptr(h), _ptr(inverse), ib,
+                                         _ptr(psi_u), psi_u.numel(), _ptr(y), _ptr(E), _ptr(norm2),
+                                         _ptr(g), _ptr(grad), _ptr(workspace),
+                                         0 if workspace is None else workspace.numel(),
+                                         _stream(stream)), "cusci_local_energy_bwd")
+    return grad
+
+
+class LocalEnergy(torch.autograd.Function):
+    """E(psi_u) in the local form of Eq. 5 over CSR coupled lists and the reverse
+    index into the distinct set, with its hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, psi_u, offsets, h, inverse):
+        E, n2, y = local_energy_fwd(offsets, h, inverse, psi_u)
+        ctx.save_for_backward(psi_u, offsets, h, inverse, E, n2, y)
+        return E.reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        psi_u, offsets, h, inverse, E, n2, y = ctx.saved_tensors
+        return local_energy_bwd(offsets, h, inverse, psi_u, E, n2, y=y, grad_out=g), None, None, None
 
 
 class Energy(torch.autograd.Function):

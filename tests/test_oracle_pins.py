@@ -225,3 +225,39 @@ def test_tiny_spectrum_golden():
     off, td, hv = O.OracleSystem.of(s).gen(s.dets, -1.0)
     H = _dense_from_lists(s.dets, off, td, hv)
     assert np.abs(np.linalg.eigvalsh(H)[:5] - ref).max() < 1e-10
+
+
+def test_local_energy_equals_variational_energy_on_closed_space():
+    """On the whole FCI space every coupled target is a source, so the local-energy
+    form (Eq. 5) equals the Rayleigh quotient over S (pinned above by eigh)."""
+    s = synth.config_system("tiny")
+    osys = O.OracleSystem.of(s)
+    off, td, hv = osys.gen(s.dets, -1.0)
+    u, inv = O.dedup(td)
+    assert np.array_equal(u, s.dets)                   # the distinct set is the space
+    rng = np.random.default_rng(4)
+    psi = rng.standard_normal(u.shape[0])
+    E_loc, n2, y, grad = O.local_energy(off, hv, inv, psi)
+    E_var, n2v, hp, gvar = osys.energy(s.dets, psi, -1.0)
+    assert abs(E_loc - E_var) <= 1e-12 * abs(E_var)
+    assert np.abs(y - hp).max() <= 1e-11
+    # on a closed space the two gradients coincide as well (H symmetric)
+    assert np.abs(grad - gvar).max() <= 1e-11
+
+
+def test_local_energy_gradient_finite_differences():
+    s = synth.config_system("mid", n_dets=60)
+    off, td, hv = O.OracleSystem.of(s).gen(s.dets, s.eps)
+    u, inv = O.dedup(td)
+    rng = np.random.default_rng(6)
+    psi = rng.standard_normal(u.shape[0]) * 0.1 + 1.0
+    E, n2, y, grad = O.local_energy(off, hv, inv, psi)
+    h = 1e-6
+    # include source entries (diagonal targets) and pure targets
+    src_ids = inv[off[:-1]]
+    picks = list(src_ids[:5]) + list(rng.choice(u.shape[0], 8, replace=False))
+    for k in picks:
+        e = np.zeros_like(psi)
+        e[k] = h
+        fd = (O.local_energy(off, hv, inv, psi + e)[0] - O.local_energy(off, hv, inv, psi - e)[0]) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-6 * max(1.0, abs(grad[k]))
