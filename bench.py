@@ -280,6 +280,34 @@ def run_ours(args):
     dom_gbs, dom_bytes, dom_ms = ((dedup_gbs, dedup_bytes, dedup_ms) if dedup_ms >= gen_ms
                                   else (gen_gbs, gen_bytes, gen_ms))
 
+    # the paper's distributed de-duplication (Sec. 4.1.1) over virtual ranks:
+    # load balance (Max/Min, CV of distinct items per rank) and throughput
+    ranks = None
+    if args.ranks:
+        del dd_ws
+        dd_ws = None
+        torch.cuda.empty_cache()
+        off_h = offsets.cpu().numpy()
+        ranks = {}
+        for P, S in ((8, 1024), (64, 256)):
+            eo = off_h[np.linspace(0, n, P + 1).astype(np.int64)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            parts, st_r, _, _, _, _ = cusci.virtual_rank_dedup(out_d, eo, P, S, n_bits, n_ones)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            ranks[f"P{P}"] = {"max_over_min": st_r["max_over_min"], "cv": st_r["cv"],
+                              "unique_max_over_min": st_r["unique_max_over_min"],
+                              "unique_cv": st_r["unique_cv"],
+                              "ms": dt * 1e3, "M_items_per_s": total / dt / 1e6,
+                              "distinct_total": int(sum(st_r["unique"]))}
+            del parts
+            torch.cuda.empty_cache()
+        ranks["workload"] = ("mid step's coupled set split by contiguous source ranges over P "
+                             "virtual ranks; max_over_min / cv of the items each rank holds "
+                             "after the exchange (the paper's metric), unique_* of its distinct "
+                             "keys")
+
     # local-energy form (Eq. 5) over this step's coupled lists and reverse index,
     # with synthetic amplitudes on the distinct set
     loc = None
@@ -365,6 +393,8 @@ def run_ours(args):
             line["energy"] = energy
         if loc is not None:
             line["local_energy"] = loc
+        if ranks is not None:
+            line["virtual_ranks"] = ranks
         if cpu is not None:
             line["cpu_baseline"] = cpu
         if stream_res is not None:
@@ -588,6 +618,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-stream", dest="stream", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-ranks", dest="ranks", action="store_false")
     ap.add_argument("--stream-sources", type=int, default=20_000)
     ap.add_argument("--stream-batch", type=int, default=16_000_000)
     ap.add_argument("--stream-unique-cap", type=int, default=400_000_000)

@@ -215,6 +215,22 @@ cusci_status cusci_local_energy_bwd(const int64_t *d_offsets, int64_t n, const d
                                     const double *d_grad_out, double *d_grad_u, void *d_ws,
                                     size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------ regular-sampling partition
+ * Steps 1 and 2 of the paper's distributed de-duplication (Sec. 4.1.1, Fig. 3)
+ * for P ranks.  d_keys: device [*][W]; run r (rank r's locally sorted distinct
+ * keys) is rows [d_run_offsets[r], d_run_offsets[r+1]) (device int64[P+1]).
+ * Each non-empty run contributes S samples at positions floor(k |run| / S),
+ * k < S; the samples are sorted and splitter j (j < P-1) is the sample at
+ * position ((j+1) * count) / P - 1 (count = number of samples), written to
+ * d_splitters (device [P-1][W]).  d_bounds (device int64 [P][P+1]) receives the
+ * cuts: rank q's share of run r is rows [bounds[r][q], bounds[r][q+1]), the keys
+ * k with splitter[q-1] < k <= splitter[q].  P * S * W must not exceed 16384
+ * (next power of two).  Step 3 (exchange and final merge) is data movement plus
+ * cusci_dedup per rank. */
+cusci_status cusci_partition_plan(const uint64_t *d_keys, int W, const int64_t *d_run_offsets,
+                                  int P, int S, uint64_t *d_splitters, int64_t *d_bounds,
+                                  void *stream);
+
 /* ------------------------------------------------------------------ streaming
  * Generation + de-duplication in mini-batches out of a caller-owned device
  * pool (Sec. 4.3: mini-batch execution, compute/transfer overlap, Stage 1

@@ -170,6 +170,46 @@ def dedup(keys, W=None):
     return uniq[:nu].copy(), inv
 
 
+def regular_sampling_plan(runs, P, S):
+    """Steps 1-2 of the sort-based regular-sampling de-duplication (Sec. 4.1.1):
+    ``runs`` is a list of P sorted distinct arrays of W-word keys ([m, W] uint64).
+    Each non-empty run gives S samples at positions floor(k m / S); the sorted
+    samples give P-1 splitters at positions ((j+1) count) // P - 1; rank q receives
+    the keys k with splitter[q-1] < k <= splitter[q].  Returns (splitters [P-1, W],
+    cuts [P, P+1] as positions into the concatenated runs)."""
+    W = runs[0].shape[1] if runs else 1
+    samples = []
+    for r in runs:
+        m = r.shape[0]
+        for k in range(S if m else 0):
+            samples.append(tuple(int(x) for x in r[(k * m) // S][::-1]))   # word W-1 first
+    samples.sort()
+    count = len(samples)
+    spl = []
+    for j in range(P - 1):
+        at = max(((j + 1) * count) // P - 1, 0)
+        spl.append(samples[at] if count else tuple([(1 << 64) - 1] * W))
+    cuts = np.zeros((P, P + 1), dtype=np.int64)
+    base = 0
+    for r_i, r in enumerate(runs):
+        keys = [tuple(int(x) for x in row[::-1]) for row in r]
+        cuts[r_i, 0] = base
+        for q in range(1, P):
+            # first position whose key exceeds splitter q-1
+            lo, hi = 0, len(keys)
+            while lo < hi:
+                mid = (lo + hi) // 2
+                if keys[mid] <= spl[q - 1]:
+                    lo = mid + 1
+                else:
+                    hi = mid
+            cuts[r_i, q] = base + lo
+        base += len(keys)
+        cuts[r_i, P] = base
+    spl_arr = np.array([list(t[::-1]) for t in spl], dtype=np.uint64).reshape(-1, W)
+    return spl_arr, cuts
+
+
 def apply_op(det, s, create):
     """(phase, new det) of a+_s (create) or a_s on one determinant."""
     d = _c(det, np.uint64).copy()

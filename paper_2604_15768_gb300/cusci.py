@@ -68,6 +68,7 @@ _PROTOS = {
     "cusci_local_energy_fwd": (_I, [_P, _I64, _P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
     "cusci_local_energy_bwd": (_I, [_P, _I64, _P, _P, _I, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ,
                                     _P]),
+    "cusci_partition_plan": (_I, [_P, _I, _P, _I, _I, _P, _P, _P]),
     "cusci_energy_workspace": (_I, [_P, _I64, ctypes.POINTER(_SZ)]),
     "cusci_energy_fwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _SZ, _P, _P]),
     "cusci_energy_bwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -418,6 +419,64 @@ def local_energy_bwd(offsets, h, inverse, psi_u, E, norm2, y=None, grad_out=None
                                          0 if workspace is None else workspace.numel(),
                                          _stream(stream)), "cusci_local_energy_bwd")
     return grad
+
+
+def partition_plan(runs: torch.Tensor, run_offsets: torch.Tensor, P: int, S: int, stream=None):
+    """Splitters [P-1, W] and cuts [P, P+1] of the regular-sampling partition of P
+    sorted distinct runs laid back to back in ``runs`` ([*, W])."""
+    W = runs.shape[1]
+    spl = torch.empty((max(P - 1, 1), W), dtype=torch.int64, device=runs.device)
+    bounds = torch.empty((P, P + 1), dtype=torch.int64, device=runs.device)
+    _check(load().cusci_partition_plan(_ptr(runs), W, _ptr(run_offsets), int(P), int(S), _ptr(spl),
+                                       _ptr(bounds), _stream(stream)), "cusci_partition_plan")
+    return spl[:P - 1], bounds
+
+
+def virtual_rank_dedup(keys: torch.Tensor, entry_offsets, P: int, S: int, n_bits: int,
+                       n_ones: int):
+    """The paper's distributed de-duplication (Sec. 4.1.1) over P virtual ranks on
+    one GPU.  Rank r owns the entries [entry_offsets[r], entry_offsets[r+1]) of
+    ``keys``.  Step 1: local sort + unique and regular sampling; Step 2: splitters
+    and cuts; Step 3: all-to-all (device copies) and a final sort + unique per
+    rank.  Returns (list of per-rank distinct partitions, stats dict)."""
+    dev = keys.device
+    W = keys.shape[1]
+    eo = [int(x) for x in entry_offsets]
+    local = []
+    for r in range(P):
+        a, b = eo[r], eo[r + 1]
+        if b > a:
+            u, _, nu = dedup(keys[a:b], n_bits, n_ones)
+            local.append(u[:nu])
+        else:
+            local.append(torch.empty((0, W), dtype=torch.int64, device=dev))
+    run_off = torch.tensor(np.concatenate([[0], np.cumsum([x.shape[0] for x in local])]),
+                           dtype=torch.int64, device=dev)
+    runs = torch.cat(local) if sum(x.shape[0] for x in local) else torch.empty((1, W),
+                                                                               dtype=torch.int64,
+                                                                               device=dev)
+    spl, bounds = partition_plan(runs, run_off, P, S)
+    bh = bounds.cpu().numpy()
+    parts, received = [], []
+    for q in range(P):
+        pieces = [runs[bh[r, q]:bh[r, q + 1]] for r in range(P) if bh[r, q + 1] > bh[r, q]]
+        recv = torch.cat(pieces) if pieces else torch.empty((0, W), dtype=torch.int64, device=dev)
+        received.append(int(recv.shape[0]))
+        if recv.shape[0]:
+            u, _, nu = dedup(recv, n_bits, n_ones)
+            parts.append(u[:nu])
+        else:
+            parts.append(recv)
+    uniq = np.array([x.shape[0] for x in parts], dtype=np.float64)
+    recv = np.array(received, dtype=np.float64)
+    # the paper's load-balance metric: items per rank after the exchange
+    stats = {"P": P, "S": S, "received": received, "unique": [int(x) for x in uniq],
+             "max_over_min": float(recv.max() / max(recv.min(), 1.0)),
+             "cv": float(recv.std() / recv.mean()) if recv.mean() > 0 else 0.0,
+             "unique_max_over_min": float(uniq.max() / max(uniq.min(), 1.0)),
+             "unique_cv": float(uniq.std() / uniq.mean()) if uniq.mean() > 0 else 0.0,
+             "local_distinct": [int(x.shape[0]) for x in local]}
+    return parts, stats, spl, bounds, runs, run_off
 
 
 class LocalEnergy(torch.autograd.Function):

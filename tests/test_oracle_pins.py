@@ -261,3 +261,33 @@ def test_local_energy_gradient_finite_differences():
         e[k] = h
         fd = (O.local_energy(off, hv, inv, psi + e)[0] - O.local_energy(off, hv, inv, psi - e)[0]) / (2 * h)
         assert abs(fd - grad[k]) <= 1e-6 * max(1.0, abs(grad[k]))
+
+
+def test_regular_sampling_plan_hand_example():
+    """Two ranks, two samples each: runs [1 3 5 7] and [2 4 6 8] sample {1, 5} and
+    {2, 6}; the sorted sample [1 2 5 6] gives the splitter at (1*4)//2 - 1 = 1,
+    i.e. the key 2, so rank 0 receives keys <= 2 and rank 1 the rest."""
+    r0 = np.array([[1], [3], [5], [7]], dtype=np.uint64)
+    r1 = np.array([[2], [4], [6], [8]], dtype=np.uint64)
+    spl, cuts = O.regular_sampling_plan([r0, r1], 2, 2)
+    assert spl.tolist() == [[2]]
+    assert cuts.tolist() == [[0, 1, 4], [4, 5, 8]]
+
+
+def test_regular_sampling_partition_covers_the_distinct_set():
+    rng = np.random.default_rng(9)
+    keys = rng.integers(0, 5000, size=(20000, 1)).astype(np.uint64)
+    P, S = 8, 16
+    runs = [O.dedup(c)[0] for c in np.array_split(keys, P)]
+    spl, cuts = O.regular_sampling_plan(runs, P, S)
+    allr = np.concatenate(runs)
+    parts = []
+    for q in range(P):
+        recv = np.concatenate([allr[cuts[r, q]:cuts[r, q + 1]] for r in range(P)])
+        u = O.dedup(recv)[0] if recv.size else recv.reshape(0, 1)
+        if q > 0 and u.size:
+            assert (u[:, 0] > spl[q - 1, 0]).all()
+        if q < P - 1 and u.size:
+            assert (u[:, 0] <= spl[q, 0]).all()
+        parts.append(u)
+    assert np.array_equal(np.concatenate(parts), O.dedup(keys)[0])
