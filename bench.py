@@ -520,6 +520,24 @@ def run_stream(args, dev):
         times.append(time.perf_counter() - t0)
     off, hd, hh, uniq, st = res
     t = min(times[1:]) if len(times) > 1 else times[0]
+    # Stage-3 reverse index of the host-resident coupled set against the device
+    # distinct set, streamed back in batches
+    total_e = st["total"]
+    h_inv = torch.empty(total_e, dtype=torch.int32).pin_memory()
+    rstatus = torch.zeros(1, dtype=torch.int32, device=dev)
+    cusci.reverse_index_stream(uniq, hd[:total_e], batch=batch, host_out=h_inv, status=rstatus)
+    rts = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cusci.reverse_index_stream(uniq, hd[:total_e], batch=batch, host_out=h_inv,
+                                   status=rstatus)
+        rts.append(time.perf_counter() - t0)
+    rt = min(rts)
+    rev = {"entries_per_s": total_e / rt, "ms": rt * 1e3,
+           "h2d_bytes": total_e * 8 * sysd.W, "d2h_bytes": total_e * 4,
+           "transfer_gbs": total_e * (8 * sysd.W + 4) / rt / 1e9,
+           "status": int(rstatus.item())}
     hbm_peak, _ = _peaks()
     # W = 2: 16 + 8 written per entry, 16 read + 4 inverse-equivalent + 16 per distinct key
     alg = st["total"] * 48 + int(uniq.shape[0]) * 16
@@ -531,8 +549,10 @@ def run_stream(args, dev):
             "pool_peak_bytes": st["pool_peak"], "batch_region_bytes": 2 * batch * 24,
             "coupled_set_bytes": st["total"] * 24, "d2h_bytes": st["d2h_bytes"],
             "d2h_gbs": st["d2h_bytes"] / t / 1e9,
+            "reverse_index": rev,
             "workload": f"large: 120 spin orbitals (2 words), 10a+10b, {s.dets.shape[0]} sources, "
-                        "eps 1e-6; host sources in, host coupled lists + device distinct set out"}
+                        "eps 1e-6; host sources in, host coupled lists + device distinct set out; "
+                        "then the reverse index of the host coupled set streamed back in"}
 
 
 def run_batched(args, dev):

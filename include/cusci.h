@@ -231,6 +231,17 @@ cusci_status cusci_partition_plan(const uint64_t *d_keys, int W, const int64_t *
                                   int P, int S, uint64_t *d_splitters, int64_t *d_bounds,
                                   void *stream);
 
+/* ------------------------------------------------------------------ reverse index
+ * Just-in-time reverse index (Stage 3 of Sec. 3, Sec. 4.3.4): d_inverse[k] =
+ * position of key k (device [n][W]) in the sorted distinct set d_unique
+ * (device [n_unique][W], as written by cusci_dedup or cusci_stream_gen_dedup),
+ * or -1 with d_status (device int32, nullable) set to CUSCI_ERR_INVALID if the
+ * key is absent.  index_bytes 4 or 8.  n_unique <= 2^29 (W = 1) or 2^28
+ * (W = 2).  Meant for batches of a host-resident coupled set streamed in. */
+cusci_status cusci_reverse_index(const uint64_t *d_unique, int64_t n_unique, int W,
+                                 const uint64_t *d_keys, int64_t n, void *d_inverse,
+                                 int index_bytes, int32_t *d_status, void *stream);
+
 /* ------------------------------------------------------------------ streaming
  * Generation + de-duplication in mini-batches out of a caller-owned device
  * pool (Sec. 4.3: mini-batch execution, compute/transfer overlap, Stage 1

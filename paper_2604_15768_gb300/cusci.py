@@ -69,6 +69,7 @@ _PROTOS = {
     "cusci_local_energy_bwd": (_I, [_P, _I64, _P, _P, _I, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ,
                                     _P]),
     "cusci_partition_plan": (_I, [_P, _I, _P, _I, _I, _P, _P, _P]),
+    "cusci_reverse_index": (_I, [_P, _I64, _I, _P, _I64, _P, _I, _P, _P]),
     "cusci_energy_workspace": (_I, [_P, _I64, ctypes.POINTER(_SZ)]),
     "cusci_energy_fwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _SZ, _P, _P]),
     "cusci_energy_bwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -419,6 +420,45 @@ def local_energy_bwd(offsets, h, inverse, psi_u, E, norm2, y=None, grad_out=None
                                          0 if workspace is None else workspace.numel(),
                                          _stream(stream)), "cusci_local_energy_bwd")
     return grad
+
+
+def reverse_index(unique: torch.Tensor, keys: torch.Tensor, index_bytes: int = 4, out=None,
+                  status=None, stream=None):
+    """Position of every key in the sorted distinct set (device tensors)."""
+    W = unique.shape[1]
+    if out is None:
+        out = torch.empty(keys.shape[0], dtype=torch.int32 if index_bytes == 4 else torch.int64,
+                          device=keys.device)
+    _check(load().cusci_reverse_index(_ptr(unique), unique.shape[0], W, _ptr(keys), keys.shape[0],
+                                      _ptr(out), index_bytes, _ptr(status), _stream(stream)),
+           "cusci_reverse_index")
+    return out
+
+
+def reverse_index_stream(unique: torch.Tensor, host_keys: torch.Tensor, batch: int,
+                         host_out: torch.Tensor | None = None, status=None):
+    """Reverse index of a host-resident (pinned) key array against the device
+    distinct set, in batches: copy in, search and copy out on two alternating
+    streams so transfers overlap the searches.  Returns the pinned host ids."""
+    n, W = host_keys.shape
+    dev = unique.device
+    if host_out is None:
+        host_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    kbuf = [torch.empty((batch, W), dtype=torch.int64, device=dev) for _ in range(2)]
+    ibuf = [torch.empty(batch, dtype=torch.int32, device=dev) for _ in range(2)]
+    torch.cuda.current_stream().synchronize()
+    for t, a in enumerate(range(0, n, batch)):
+        b = min(n, a + batch)
+        s = streams[t & 1]
+        with torch.cuda.stream(s):
+            kb, ib = kbuf[t & 1][:b - a], ibuf[t & 1][:b - a]
+            kb.copy_(host_keys[a:b], non_blocking=True)
+            reverse_index(unique, kb, 4, out=ib, status=status, stream=s)
+            host_out[a:b].copy_(ib, non_blocking=True)
+    for s in streams:
+        s.synchronize()
+    return host_out
 
 
 def partition_plan(runs: torch.Tensor, run_offsets: torch.Tensor, P: int, S: int, stream=None):
