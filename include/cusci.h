@@ -242,6 +242,20 @@ cusci_status cusci_reverse_index(const uint64_t *d_unique, int64_t n_unique, int
                                  const uint64_t *d_keys, int64_t n, void *d_inverse,
                                  int index_bytes, int32_t *d_status, void *stream);
 
+/* ------------------------------------------------------------------ top-K selection
+ * Streaming two-level top-K (Stage 2 of Sec. 3, the running best set of
+ * Sec. 4.3.4): merges one batch (d_scores / d_ids, device, n items; scores
+ * non-negative FP64, ids distinct) into the running best set d_best_scores /
+ * d_best_ids (device, capacity K, count in device int64 *d_best_count; start
+ * it at 0).  The batch's own K best are selected first, then merged with the
+ * running set.  Best = larger score, equal scores by smaller id (exact and
+ * deterministic); the running set is kept unordered.  Workspace:
+ * cusci_topk_workspace(n, K) bytes, 256-byte aligned.  No host synchronisation. */
+cusci_status cusci_topk_workspace(int64_t batch, int64_t K, size_t *bytes);
+cusci_status cusci_topk_update(const double *d_scores, const int64_t *d_ids, int64_t n, int64_t K,
+                               double *d_best_scores, int64_t *d_best_ids,
+                               int64_t *d_best_count, void *d_ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------ streaming
  * Generation + de-duplication in mini-batches out of a caller-owned device
  * pool (Sec. 4.3: mini-batch execution, compute/transfer overlap, Stage 1

@@ -70,6 +70,8 @@ _PROTOS = {
                                     _P]),
     "cusci_partition_plan": (_I, [_P, _I, _P, _I, _I, _P, _P, _P]),
     "cusci_reverse_index": (_I, [_P, _I64, _I, _P, _I64, _P, _I, _P, _P]),
+    "cusci_topk_workspace": (_I, [_I64, _I64, ctypes.POINTER(_SZ)]),
+    "cusci_topk_update": (_I, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, _P]),
     "cusci_energy_workspace": (_I, [_P, _I64, ctypes.POINTER(_SZ)]),
     "cusci_energy_fwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _SZ, _P, _P]),
     "cusci_energy_bwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -459,6 +461,37 @@ def reverse_index_stream(unique: torch.Tensor, host_keys: torch.Tensor, batch: i
     for s in streams:
         s.synchronize()
     return host_out
+
+
+class TopK:
+    """Running best-K set over a stream of scored batches (device resident)."""
+
+    def __init__(self, K: int, max_batch: int, device="cuda"):
+        self.K = int(K)
+        self.scores = torch.zeros(self.K, dtype=torch.float64, device=device)
+        self.ids = torch.zeros(self.K, dtype=torch.int64, device=device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=device)
+        ws = ctypes.c_size_t()
+        _check(load().cusci_topk_workspace(int(max_batch), self.K, ctypes.byref(ws)),
+               "cusci_topk_workspace")
+        self.ws = torch.empty(ws.value, dtype=torch.uint8, device=device)
+        self.max_batch = int(max_batch)
+
+    def update(self, scores: torch.Tensor, ids: torch.Tensor, stream=None):
+        n = scores.shape[0]
+        if n > self.max_batch:
+            raise ValueError("batch larger than max_batch")
+        _check(load().cusci_topk_update(_ptr(scores), _ptr(ids), n, self.K, _ptr(self.scores),
+                                        _ptr(self.ids), _ptr(self.count), _ptr(self.ws),
+                                        self.ws.numel(), _stream(stream)), "cusci_topk_update")
+
+    def result(self):
+        """(scores, ids) of the best set, best first (host numpy)."""
+        c = int(self.count.item())
+        sc = self.scores[:c].cpu().numpy()
+        ids = self.ids[:c].cpu().numpy()
+        order = np.lexsort((ids, -sc))
+        return sc[order], ids[order]
 
 
 def partition_plan(runs: torch.Tensor, run_offsets: torch.Tensor, P: int, S: int, stream=None):
