@@ -55,6 +55,8 @@ def _lib():
             lib.orc_dedup.argtypes = [P, I64, I, P, P]
             lib.orc_hpsi.restype = None
             lib.orc_hpsi.argtypes = [I, I, I, P, P, D, P, I64, P, D, P]
+            lib.orc_hpsi_rows.restype = None
+            lib.orc_hpsi_rows.argtypes = [I, I, I, P, P, D, P, I64, P, D, P, I64, P]
             lib.orc_energy_reduce.restype = None
             lib.orc_energy_reduce.argtypes = [P, P, I64, P, P]
             lib.orc_energy_grad.restype = None
@@ -123,6 +125,18 @@ class OracleSystem:
         psi = _c(psi, np.float64)
         out = np.zeros(S.shape[0], dtype=np.float64)
         _lib().orc_hpsi(*self._head(), _p(S), S.shape[0], _p(psi), float(eps), _p(out))
+        return out
+
+    def hpsi_rows(self, S, psi, eps, rows):
+        """(H psi)_i restricted to S for the chosen rows i of S only (same loop
+        as ``hpsi``, so a sample of a large S can be checked)."""
+        S = _c(S, np.uint64).reshape(-1, self.W)
+        psi = _c(psi, np.float64)
+        rows = _c(rows, np.int64)
+        assert rows.size == 0 or (rows.min() >= 0 and rows.max() < S.shape[0])
+        out = np.zeros(rows.size, dtype=np.float64)
+        _lib().orc_hpsi_rows(*self._head(), _p(S), S.shape[0], _p(psi), float(eps), _p(rows),
+                             rows.size, _p(out))
         return out
 
     def energy(self, S, psi, eps, g=1.0):

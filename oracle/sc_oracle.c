@@ -264,35 +264,61 @@ static void nm_add(neumaier *a, double x) {
 }
 static double nm_value(const neumaier *a) { return a->sum + a->comp; }
 
+/* (H psi)_i restricted to S (Eq. 1 with j running over S only) for one row i
+ * of the sorted unique set S: every entry of C_i, in canonical order, whose
+ * target is found in S by binary search contributes H_ij psi_j.  dbuf / hbuf
+ * (capacity *cap entries) are grown as needed. */
+static double hpsi_row(const orc_sys *s, const uint64_t *S, int64_t nS, const double *psi,
+                       double eps, int64_t i, uint64_t **dbuf, double **hbuf, int64_t *cap) {
+    const int W = s->W;
+    sink c = {NULL, NULL, 0, W};
+    coupled_one(s, S + (size_t)i * W, eps, &c);
+    if (c.n > *cap) {
+        *cap = c.n;
+        *dbuf = (uint64_t *)realloc(*dbuf, sizeof(uint64_t) * W * *cap);
+        *hbuf = (double *)realloc(*hbuf, sizeof(double) * *cap);
+    }
+    sink z = {*dbuf, *hbuf, 0, W};
+    coupled_one(s, S + (size_t)i * W, eps, &z);
+    double acc = 0.0;
+    for (int64_t e = 0; e < z.n; e++) {
+        const uint64_t *jd = *dbuf + (size_t)e * W;
+        int64_t j = lower_bound_words(S, nS, jd, W);
+        if (j < nS && cmp_words(S + (size_t)j * W, jd, W) == 0) acc += (*hbuf)[e] * psi[j];
+    }
+    return acc;
+}
+
 /* (H psi)_i restricted to S, for every i of the sorted unique set S */
 void orc_hpsi(int norb, int na, int nb, const double *h1, const double *h2, double ecore,
               const uint64_t *S, int64_t nS, const double *psi, double eps, double *hpsi) {
     orc_sys s = make_sys(norb, na, nb, h1, h2, ecore);
-    const int W = s.W;
 #pragma omp parallel
     {
         int64_t cap = 1 << 16;
-        uint64_t *dbuf = (uint64_t *)malloc(sizeof(uint64_t) * W * cap);
+        uint64_t *dbuf = (uint64_t *)malloc(sizeof(uint64_t) * s.W * cap);
         double *hbuf = (double *)malloc(sizeof(double) * cap);
 #pragma omp for schedule(dynamic, 16)
-        for (int64_t i = 0; i < nS; i++) {
-            sink c = {NULL, NULL, 0, W};
-            coupled_one(&s, S + (size_t)i * W, eps, &c);
-            if (c.n > cap) {
-                cap = c.n;
-                dbuf = (uint64_t *)realloc(dbuf, sizeof(uint64_t) * W * cap);
-                hbuf = (double *)realloc(hbuf, sizeof(double) * cap);
-            }
-            sink z = {dbuf, hbuf, 0, W};
-            coupled_one(&s, S + (size_t)i * W, eps, &z);
-            double acc = 0.0;
-            for (int64_t e = 0; e < z.n; e++) {
-                const uint64_t *jd = dbuf + (size_t)e * W;
-                int64_t j = lower_bound_words(S, nS, jd, W);
-                if (j < nS && cmp_words(S + (size_t)j * W, jd, W) == 0) acc += hbuf[e] * psi[j];
-            }
-            hpsi[i] = acc;
-        }
+        for (int64_t i = 0; i < nS; i++)
+            hpsi[i] = hpsi_row(&s, S, nS, psi, eps, i, &dbuf, &hbuf, &cap);
+        free(dbuf);
+        free(hbuf);
+    }
+}
+
+/* the same (H psi)_i for the chosen rows only: out[r] = (H psi)_{rows[r]} */
+void orc_hpsi_rows(int norb, int na, int nb, const double *h1, const double *h2, double ecore,
+                   const uint64_t *S, int64_t nS, const double *psi, double eps,
+                   const int64_t *rows, int64_t nrows, double *out) {
+    orc_sys s = make_sys(norb, na, nb, h1, h2, ecore);
+#pragma omp parallel
+    {
+        int64_t cap = 1 << 16;
+        uint64_t *dbuf = (uint64_t *)malloc(sizeof(uint64_t) * s.W * cap);
+        double *hbuf = (double *)malloc(sizeof(double) * cap);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t r = 0; r < nrows; r++)
+            out[r] = hpsi_row(&s, S, nS, psi, eps, rows[r], &dbuf, &hbuf, &cap);
         free(dbuf);
         free(hbuf);
     }

@@ -184,6 +184,29 @@ def test_energy_gradient_finite_difference_and_invariants():
             if j is not None:
                 ref[i] += hv[e_] * psi[j]
     assert np.abs(ref - hp).max() <= 1e-12 * np.abs(ref).max()
+    # the row-subset form (for samples of a large S) against the same product
+    rows = np.concatenate([[0, S.shape[0] - 1], rng.choice(S.shape[0], 40, replace=False)])
+    hr = osys.hpsi_rows(S, psi, s.eps, rows)
+    assert np.abs(hr - ref[rows]).max() <= 1e-12 * np.abs(ref).max()
+    assert np.array_equal(hr, hp[rows])
+
+
+def test_hpsi_rows_two_words_against_dense_product():
+    s = synth.config_system("large", n_dets=60)
+    S = s.dets[np.lexsort([s.dets[:, w] for w in range(s.dets.shape[1])])]
+    osys = O.OracleSystem.of(s)
+    psi = np.random.default_rng(8).standard_normal(S.shape[0])
+    off, td, hv = osys.gen(S, s.eps)
+    pos = {tuple(r): i for i, r in enumerate(S.tolist())}
+    ref = np.zeros(S.shape[0])
+    for i in range(S.shape[0]):
+        for e_ in range(off[i], off[i + 1]):
+            j = pos.get(tuple(td[e_].tolist()))
+            if j is not None:
+                ref[i] += hv[e_] * psi[j]
+    rows = np.array([59, 3, 17, 0, 42], dtype=np.int64)
+    hr = osys.hpsi_rows(S, psi, s.eps, rows)
+    assert np.abs(hr - ref[rows]).max() <= 1e-12 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("W", [1, 2])
