@@ -81,6 +81,11 @@ uint64_t cusci_kernel_launches(void);
  * FP64 slabs plus per-eps screening bitmasks).  h1: host, norb*norb doubles.
  * h2: host, norb^4 doubles.  Both are copied; the caller may free them on
  * return.  1 <= norb <= 64, 0 <= n_alpha, n_beta <= norb.  Synchronous.
+ * The system caches the screening masks of the four most recently used eps
+ * values; a call at a fifth eps rebuilds the least recently used set in place
+ * after waiting for all earlier work on the device (calls on other streams may
+ * still read it), and fails with CUSCI_ERR_INVALID if its stream is being
+ * captured into a CUDA graph (run each eps once before capturing).
  * Errors: CUSCI_ERR_INVALID (sizes), CUSCI_ERR_OOM, CUSCI_ERR_CUDA. */
 cusci_status cusci_system_create(int norb, int n_alpha, int n_beta, const double *h1,
                                  const double *h2, double ecore, cusci_system **out);
@@ -249,12 +254,16 @@ cusci_status cusci_reverse_index(const uint64_t *d_unique, int64_t n_unique, int
  * d_best_ids (device, capacity K, count in device int64 *d_best_count; start
  * it at 0).  The batch's own K best are selected first, then merged with the
  * running set.  Best = larger score, equal scores by smaller id (exact and
- * deterministic); the running set is kept unordered.  Workspace:
- * cusci_topk_workspace(n, K) bytes, 256-byte aligned.  No host synchronisation. */
+ * deterministic); the running set is kept unordered; -0.0 counts as 0.
+ * d_status (device int32, nullable): set to CUSCI_ERR_INVALID if a score of the
+ * batch is negative or NaN (the selection is then not meaningful).
+ * Workspace: cusci_topk_workspace(n, K) bytes, 256-byte aligned.  No host
+ * synchronisation. */
 cusci_status cusci_topk_workspace(int64_t batch, int64_t K, size_t *bytes);
 cusci_status cusci_topk_update(const double *d_scores, const int64_t *d_ids, int64_t n, int64_t K,
                                double *d_best_scores, int64_t *d_best_ids,
-                               int64_t *d_best_count, void *d_ws, size_t ws_bytes, void *stream);
+                               int64_t *d_best_count, void *d_ws, size_t ws_bytes,
+                               int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------ streaming
  * Generation + de-duplication in mini-batches out of a caller-owned device
@@ -275,6 +284,19 @@ cusci_status cusci_topk_update(const double *d_scores, const int64_t *d_ids, int
  * batch), CUSCI_ERR_OVERFLOW (more distinct keys than unique_capacity),
  * CUSCI_ERR_TIMEOUT (a bounded wait in the hash set gave up),
  * CUSCI_ERR_UNSUPPORTED (64 or more electrons). */
+/* The streaming path's device hash set, exposed so that its bounded wait can
+ * be exercised (the failure tier of the tests; no counterpart in the paper).
+ * Inserts the n keys d_keys (device [n][W]) into d_table (device [slots][W],
+ * slots a power of two, empty slots all ones) by open addressing; *d_n_new
+ * (device, accumulated) counts keys not present before.  A two-word insert
+ * that finds its first word already claimed polls the slot's second word at
+ * most spin_limit times (the streaming path uses 2^20); if it is still empty
+ * then, d_status (device int32, nullable) receives CUSCI_ERR_TIMEOUT and the
+ * key is dropped -- no wait is unbounded.  A full table gives
+ * CUSCI_ERR_OVERFLOW.  Asynchronous on the stream. */
+cusci_status cusci_hash_insert_probe(const uint64_t *d_keys, int64_t n, int W, uint64_t *d_table,
+                                     int64_t slots, int spin_limit, unsigned long long *d_n_new,
+                                     int32_t *d_status, void *stream);
 cusci_status cusci_stream_pool_bytes(const cusci_system *sys, int64_t n_sources,
                                      int64_t batch_entries, int64_t unique_capacity,
                                      size_t *bytes);
@@ -295,9 +317,11 @@ cusci_status cusci_stream_gen_dedup(const cusci_system *sys, const uint64_t *h_d
  * a zero high word); targets are written the same way into one CSR over all
  * sources.  cusci_batch_create: systems stay owned by the caller and must
  * outlive the batch; h_sources[k] = number of sources of system k; chunk =
- * sources per work item (cusci_batch_set_chunk changes it).  The first count
- * or gen call at a new eps builds the systems' screening masks and
- * synchronizes the stream; later calls at the same eps are plain asynchronous
+ * sources per work item (cusci_batch_set_chunk changes it).  The batch owns
+ * its own screening masks, one set per system, so calls on the systems
+ * themselves never change what a batch launch (or a graph replay of one)
+ * reads.  The first count or gen call at a new eps synchronizes the stream and
+ * rebuilds those masks; later calls at the same eps are plain asynchronous
  * launches (capturable in a CUDA graph).  Per-system de-duplication is
  * cusci_dedup on each system's slice of the targets. */
 typedef struct cusci_batch cusci_batch;

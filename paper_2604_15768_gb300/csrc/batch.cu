@@ -24,6 +24,8 @@ struct cusci_batch {
     std::vector<const cusci_system *> systems;
     std::vector<int64_t> src_begin;  // n_sys + 1, global source index of each system
     double eps;                      // eps the masks below were built for (NaN: none)
+    std::vector<uint64_t *> masks;   // device screening masks of every system, owned by the
+                                     // batch (graph replays never see another call's eps)
     cusci::SysView *d_views;         // device [n_sys]
     int4 *d_items;                   // device work list: (system, first, count, unused)
     int n_items;
@@ -146,16 +148,18 @@ cusci_status refresh_views(cusci_batch *b, double eps, cudaStream_t st) {
     uint64_t want, have;
     memcpy(&want, &eps, 8);
     memcpy(&have, &b->eps, 8);
-    if (want == have && b->d_views) return CUSCI_OK;
+    if (want == have) return CUSCI_OK;
+    // the previous launches may still read the masks being rebuilt
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: drain before rebuilding masks");
     std::vector<SysView> views(b->n_sys);
     for (int k = 0; k < b->n_sys; k++) {
-        const uint64_t *mask = NULL;
-        cusci_status rc = masks_for(const_cast<cusci_system *>(b->systems[k]), eps, st, &mask);
+        cusci_status rc = build_masks_into(b->systems[k], eps, st, b->masks[k]);
         if (rc != CUSCI_OK) return rc;
-        views[k] = view_of(b->systems[k], mask);
+        views[k] = view_of(b->systems[k], b->masks[k]);
     }
-    cudaError_t e = cudaMemcpyAsync(b->d_views, views.data(), sizeof(SysView) * b->n_sys,
-                                    cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(b->d_views, views.data(), sizeof(SysView) * b->n_sys,
+                        cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "batch: views");
     b->eps = eps;
@@ -215,8 +219,11 @@ extern "C" cusci_status cusci_batch_create(const cusci_system *const *systems, i
     b->d_views = NULL;
     b->d_items = NULL;
     b->d_counter = NULL;
+    b->masks.assign(n_systems, NULL);
     cudaError_t e = cudaMalloc(&b->d_views, sizeof(SysView) * n_systems);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(unsigned int));
+    for (int k = 0; k < n_systems && e == cudaSuccess; k++)
+        e = cudaMalloc(&b->masks[k], mask_words(systems[k]) * sizeof(uint64_t));
     if (e != cudaSuccess) {
         cusci_batch_destroy(b);
         return cuda_fail(e, "cusci_batch_create: cudaMalloc");
@@ -235,6 +242,7 @@ extern "C" void cusci_batch_destroy(cusci_batch *b) {
     cudaFree(b->d_views);
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
+    for (uint64_t *m : b->masks) cudaFree(m);
     delete b;
 }
 

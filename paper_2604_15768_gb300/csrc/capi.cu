@@ -1,7 +1,10 @@
 // Error reporting and version of the C ABI.
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <stdarg.h>
 #include <stdio.h>
+#include <utility>
 
 #include "cusci_internal.cuh"
 
@@ -25,6 +28,25 @@ cusci_status fail(cusci_status st, const char *fmt, ...) {
 cusci_status cuda_fail(cudaError_t e, const char *what) {
     return fail(e == cudaErrorMemoryAllocation ? CUSCI_ERR_OOM : CUSCI_ERR_CUDA, "%s: %s (%s)",
                 what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The attribute is per (function, device); the largest value
+// set so far is remembered under a lock, so concurrent callers and several
+// devices are safe.
+cusci_status allow_smem(const void *fn, size_t bytes, const char *what) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &have = done[std::make_pair(fn, dev)];
+    if (have >= bytes) return CUSCI_OK;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    have = bytes;
+    return CUSCI_OK;
 }
 
 }  // namespace cusci

@@ -144,14 +144,9 @@ cusci_status launch_fill(const SysView &v, const uint64_t *d_dets, int64_t n, do
                          int32_t *d_status, cudaStream_t st) {
     const size_t smem = (size_t)WARPS_PER_BLOCK * stage_bytes(v.slab, v.mrow);
     if (W == 1 && smem <= 200 * 1024 && fill_stage_default()) {
-        static size_t attr = 0;
-        if (attr < smem) {
-            cudaError_t e = cudaFuncSetAttribute(fill_kernel<W, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return cuda_fail(e, "fill: shared-memory attribute");
-            attr = smem;
-        }
+        cusci_status rc = allow_smem((const void *)fill_kernel<W, true>, smem,
+                                     "fill: shared-memory attribute");
+        if (rc != CUSCI_OK) return rc;
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, fill_kernel<W, true>, 32 * WARPS_PER_BLOCK, smem);

@@ -52,9 +52,19 @@ void note_launches(int n);
 cusci_status fail(cusci_status st, const char *fmt, ...);
 cusci_status cuda_fail(cudaError_t e, const char *what);
 
+// raises fn's dynamic shared-memory limit to >= bytes on the current device
+// (once per function and device, thread-safe)
+cusci_status allow_smem(const void *fn, size_t bytes, const char *what);
+
 // returns the screening masks for eps, building them on `stream` if needed
+// (the system keeps CUSCI_MASK_SLOTS of them, least recently used replaced;
+// replacing one first waits for the device's earlier work)
 cusci_status masks_for(cusci_system *sys, double eps, cudaStream_t stream,
                        const uint64_t **out);
+// words of one set of screening masks, and a build of one into caller memory
+size_t mask_words(const cusci_system *sys);
+cusci_status build_masks_into(const cusci_system *sys, double eps, cudaStream_t stream,
+                              uint64_t *bits);
 
 // device view of a system for kernels
 struct SysView {

@@ -20,6 +20,8 @@
 
 #include <string.h>
 
+#include <mutex>
+
 #include "radix.cuh"
 
 namespace cusci {
@@ -260,9 +262,12 @@ __global__ void widen_hist(const uint32_t *__restrict__ h, int64_t n, int64_t *_
 }
 
 cusci_status ensure_binom() {
+    static std::mutex mu;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && g_binom_ready[dev]) return CUSCI_OK;
+    if (dev < 0 || dev >= 64) return fail(CUSCI_ERR_INVALID, "dedup: device id out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (g_binom_ready[dev]) return CUSCI_OK;
     static uint64_t host[128 * BINOM_K];
     static ulonglong2 host2[128 * BINOM_K];
     static unsigned __int128 pas[128][BINOM_K];
@@ -279,7 +284,7 @@ cusci_status ensure_binom() {
     cudaError_t e = cudaMemcpyToSymbol(g_binom, host, sizeof(host));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_binom2, host2, sizeof(host2));
     if (e != cudaSuccess) return cuda_fail(e, "dedup: binomial table upload");
-    if (dev < 64) g_binom_ready[dev] = true;
+    g_binom_ready[dev] = true;
     return CUSCI_OK;
 }
 
@@ -300,12 +305,9 @@ cusci_status run_dedup(const Plan &p, const uint64_t *d_keys, int64_t total, int
                                                     d_status);
     CUSCI_LAUNCHED(1, "dedup prepare");
     const size_t smem = sizeof(DownSmem<KW>);
-    static bool attr_set[3] = {false, false, false};
-    if (!attr_set[KW]) {
-        cudaError_t e = cudaFuncSetAttribute(downsweep<KW>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "dedup: smem attribute");
-        attr_set[KW] = true;
+    {
+        cusci_status rc = allow_smem((const void *)downsweep<KW>, smem, "dedup: smem attribute");
+        if (rc != CUSCI_OK) return rc;
     }
     const int64_t nh = (int64_t)RADIX * p.grid;
     for (int pass = 0; pass < p.passes; pass++) {

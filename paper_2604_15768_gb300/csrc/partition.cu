@@ -142,14 +142,11 @@ extern "C" cusci_status cusci_partition_plan(const uint64_t *d_keys, int W,
                     MAX_SAMPLE_WORDS);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t smem = (size_t)n2 * W * 8;
-    static bool attr[3] = {false, false, false};
-    if (!attr[W]) {
-        cudaError_t e = cudaFuncSetAttribute(W == 1 ? (const void *)sample_sort_splitters<1>
-                                                    : (const void *)sample_sort_splitters<2>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             MAX_SAMPLE_WORDS * 8);
-        if (e != cudaSuccess) return cuda_fail(e, "cusci_partition_plan: smem attribute");
-        attr[W] = true;
+    {
+        cusci_status rc = allow_smem(W == 1 ? (const void *)sample_sort_splitters<1>
+                                            : (const void *)sample_sort_splitters<2>,
+                                     MAX_SAMPLE_WORDS * 8, "cusci_partition_plan: smem attribute");
+        if (rc != CUSCI_OK) return rc;
     }
     if (P > 1) {
         if (W == 1)

@@ -61,13 +61,10 @@ cusci_status launch_rev(const uint64_t *uniq, int64_t nu, const uint64_t *keys, 
                         void *inverse, int32_t *status, cudaStream_t st) {
     const int64_t ntop = (nu + (1ll << LOG_STEP) - 1) >> LOG_STEP;
     const size_t smem = (size_t)ntop * W * 8;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(reverse_kernel<W, IDX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             MAX_INDEX_WORDS * 8);
-        if (e != cudaSuccess) return cuda_fail(e, "reverse index: smem attribute");
-        attr = true;
+    {
+        cusci_status rc = allow_smem((const void *)reverse_kernel<W, IDX>, MAX_INDEX_WORDS * 8,
+                                     "reverse index: smem attribute");
+        if (rc != CUSCI_OK) return rc;
     }
     int64_t blocks = (n + RT2 - 1) / RT2;
     if (blocks > sm_count() * 8) blocks = sm_count() * 8;

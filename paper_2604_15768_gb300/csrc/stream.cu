@@ -30,6 +30,10 @@ namespace {
 
 constexpr uint64_t EMPTY = ~0ull;
 constexpr int HT = 256;
+// polls of a slot's second key word before a two-word insert gives up
+// (another thread has claimed the slot's first word and writes the second
+// right after)
+constexpr int SPIN_LIMIT = 1 << 20;
 
 __device__ __forceinline__ uint64_t mix64s(uint64_t x) {
     x ^= x >> 31;
@@ -44,7 +48,7 @@ template <int W>
 __global__ void __launch_bounds__(HT)
     hash_insert(const uint64_t *__restrict__ keys, int64_t n, uint64_t *__restrict__ tab,
                 uint64_t mask, unsigned long long *__restrict__ n_new,
-                int32_t *__restrict__ status) {
+                int32_t *__restrict__ status, int spin_limit) {
     unsigned long long mine = 0;
     for (int64_t k = blockIdx.x * (int64_t)HT + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * HT) {
@@ -68,7 +72,7 @@ __global__ void __launch_bounds__(HT)
                     done = true;
                 } else {
                     uint64_t second = EMPTY;
-                    for (int spin = 0; spin < (1 << 20); spin++) {
+                    for (int spin = 0; spin < spin_limit; spin++) {
                         second = *(volatile uint64_t *)(slot + 1);
                         if (second != EMPTY) break;
                     }
@@ -284,9 +288,11 @@ extern "C" cusci_status cusci_stream_gen_dedup(
         if (blocks > sm_count() * 8) blocks = sm_count() * 8;
         if (blocks < 1) blocks = 1;
         if (W == 1)
-            hash_insert<1><<<blocks, HT, 0, st>>>(bd[buf], be, tab, slots - 1, d_ctr, d_status);
+            hash_insert<1><<<blocks, HT, 0, st>>>(bd[buf], be, tab, slots - 1, d_ctr, d_status,
+                                                  SPIN_LIMIT);
         else
-            hash_insert<2><<<blocks, HT, 0, st>>>(bd[buf], be, tab, slots - 1, d_ctr, d_status);
+            hash_insert<2><<<blocks, HT, 0, st>>>(bd[buf], be, tab, slots - 1, d_ctr, d_status,
+                                                  SPIN_LIMIT);
         e = cudaGetLastError();
         if (e != cudaSuccess) { rc = cuda_fail(e, "stream: hash insert"); break; }
         note_launches(1);
@@ -359,5 +365,27 @@ extern "C" cusci_status cusci_stream_gen_dedup(
         h_stats[2] = (int64_t)(peak1 > peak2 ? peak1 : peak2);
         h_stats[3] = offload ? total * (8 * W + 8) : 0;
     }
+    return CUSCI_OK;
+}
+
+extern "C" cusci_status cusci_hash_insert_probe(const uint64_t *d_keys, int64_t n, int W,
+                                                uint64_t *d_table, int64_t slots, int spin_limit,
+                                                unsigned long long *d_n_new, int32_t *d_status,
+                                                void *stream) {
+    if (n < 0 || (W != 1 && W != 2) || slots < 1 || (slots & (slots - 1)) || spin_limit < 0)
+        return fail(CUSCI_ERR_INVALID, "cusci_hash_insert_probe: bad argument");
+    if (n == 0) return CUSCI_OK;
+    if (!d_keys || !d_table || !d_n_new)
+        return fail(CUSCI_ERR_INVALID, "cusci_hash_insert_probe: NULL buffer");
+    int blocks = (int)((n + HT - 1) / HT);
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (W == 1)
+        hash_insert<1><<<blocks, HT, 0, st>>>(d_keys, n, d_table, (uint64_t)(slots - 1), d_n_new,
+                                              d_status, spin_limit);
+    else
+        hash_insert<2><<<blocks, HT, 0, st>>>(d_keys, n, d_table, (uint64_t)(slots - 1), d_n_new,
+                                              d_status, spin_limit);
+    CUSCI_LAUNCHED(1, "hash insert probe");
     return CUSCI_OK;
 }

@@ -77,6 +77,20 @@ __global__ void build_masks(int n, int slab, int mrow, const double *__restrict_
 
 }  // namespace
 
+size_t mask_words(const cusci_system *sys) {
+    return 2 * (size_t)sys->norb * sys->norb * sys->mrow;
+}
+
+cusci_status build_masks_into(const cusci_system *sys, double eps, cudaStream_t stream,
+                              uint64_t *bits) {
+    const size_t rows = mask_words(sys);
+    int blocks = (int)((rows + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    build_masks<<<blocks, 256, 0, stream>>>(sys->norb, sys->slab, sys->mrow, sys->T, eps, bits);
+    CUSCI_LAUNCHED(1, "build_masks");
+    return CUSCI_OK;
+}
+
 cusci_status masks_for(cusci_system *sys, double eps, cudaStream_t stream, const uint64_t **out) {
     uint64_t eps_bits;
     memcpy(&eps_bits, &eps, 8);
@@ -100,16 +114,26 @@ cusci_status masks_for(cusci_system *sys, double eps, cudaStream_t stream, const
             if (sys->masks[k].stamp < sys->masks[victim].stamp) victim = k;
     }
     MaskSlot &m = sys->masks[victim];
-    const int n = sys->norb;
-    const size_t rows = 2 * (size_t)n * n * sys->mrow;
+    if (m.valid) {
+        // The slot is rebuilt in place: kernels of earlier calls, on any stream,
+        // may still read it, so they must finish first.  Not possible while a
+        // stream is being captured (warm the four slots up before capturing).
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+        if (e != cudaSuccess) return cuda_fail(e, "screening masks: capture query");
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(CUSCI_ERR_INVALID,
+                        "screening masks: a fifth eps on one system during graph capture");
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "screening masks: drain before rebuild");
+        m.valid = false;
+    }
     if (!m.bits) {
-        cudaError_t e = cudaMalloc(&m.bits, rows * sizeof(uint64_t));
+        cudaError_t e = cudaMalloc(&m.bits, mask_words(sys) * sizeof(uint64_t));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(screening masks)");
     }
-    int blocks = (int)((rows + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
-    build_masks<<<blocks, 256, 0, stream>>>(n, sys->slab, sys->mrow, sys->T, eps, m.bits);
-    CUSCI_LAUNCHED(1, "build_masks");
+    cusci_status rc = build_masks_into(sys, eps, stream, m.bits);
+    if (rc != CUSCI_OK) return rc;
     m.eps = eps;
     m.valid = true;
     m.stamp = ++sys->clock;

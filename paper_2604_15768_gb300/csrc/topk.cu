@@ -10,7 +10,7 @@
 // one-thread pick of the digit holding the K-th key; the items below the
 // selected key, plus the key itself, are then compacted.  Scores are
 // non-negative FP64 (e.g. |psi| or psi^2); their bit patterns order as their
-// values do.
+// values do once -0.0 is read as +0.0.
 
 #include "cusci_internal.cuh"
 
@@ -30,8 +30,12 @@ struct SelState {
     int pad;
 };
 
+// Composite key of an item: inverted score bits (larger score -> smaller key),
+// then the id.  Adding +0.0 first turns -0.0 into +0.0, whose bit pattern is
+// the smallest of all non-negative scores (the sign bit of -0.0 would rank it
+// above every positive score).
 __device__ __forceinline__ void comp_key(double score, int64_t id, uint64_t &hi, uint64_t &lo) {
-    hi = ~(uint64_t)__double_as_longlong(score);  // larger score -> smaller key
+    hi = ~(uint64_t)__double_as_longlong(__dadd_rn(score, 0.0));
     lo = (uint64_t)id;
 }
 
@@ -68,7 +72,7 @@ __global__ void __launch_bounds__(KT)
     sel_hist(const double *__restrict__ sc, const int64_t *__restrict__ id, int64_t n,
              const int64_t *__restrict__ n1p, const double *__restrict__ sc2, const int64_t *__restrict__ id2,
              const int64_t *__restrict__ n2p, const SelState *__restrict__ st, int pass,
-             unsigned int *__restrict__ hist) {
+             unsigned int *__restrict__ hist, int32_t *__restrict__ status) {
     __shared__ unsigned int h[256];
     for (int d = threadIdx.x; d < 256; d += KT) h[d] = 0;
     __syncthreads();
@@ -80,8 +84,10 @@ __global__ void __launch_bounds__(KT)
     for (int64_t k = blockIdx.x * (int64_t)KT + threadIdx.x; k < tot;
          k += (int64_t)gridDim.x * KT) {
         uint64_t hi, lo;
-        if (k < n1) comp_key(sc[k], id[k], hi, lo);
-        else comp_key(sc2[k - n1], id2[k - n1], hi, lo);
+        const double v = k < n1 ? sc[k] : sc2[k - n1];
+        comp_key(v, k < n1 ? id[k] : id2[k - n1], hi, lo);
+        // negative or NaN scores do not order by their bits: reported
+        if (pass == 0 && status && !(v >= 0.0)) *status = CUSCI_ERR_INVALID;
         if (tied(hi, lo, s)) atomicAdd(&h[digit_at(hi, lo, pass)], 1u);
     }
     __syncthreads();
@@ -203,7 +209,7 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 cusci_status select_best(const double *sc, const int64_t *id, int64_t n, const int64_t *n1p,
                          const double *sc2, const int64_t *id2, const int64_t *n2p, int64_t n2max,
                          int64_t K, double *out_sc, int64_t *out_id, int64_t *out_n,
-                         unsigned char *ws, cudaStream_t st) {
+                         unsigned char *ws, int32_t *status, cudaStream_t st) {
     SelState *state = (SelState *)ws;
     unsigned int *hist = (unsigned int *)(ws + 256);
     const int64_t tot_max = n + n2max;
@@ -216,7 +222,7 @@ cusci_status select_best(const double *sc, const int64_t *id, int64_t n, const i
     if (hb > sm_count() * 8) hb = sm_count() * 8;
     if (hb < 1) hb = 1;
     for (int pass = 0; pass < 16; pass++) {
-        sel_hist<<<hb, KT, 0, st>>>(sc, id, n, n1p, sc2, id2, n2p, state, pass, hist);
+        sel_hist<<<hb, KT, 0, st>>>(sc, id, n, n1p, sc2, id2, n2p, state, pass, hist, status);
         sel_pick<<<1, 256, 0, st>>>(state, pass, hist);
     }
     sel_count<<<(unsigned)tiles, KT, 0, st>>>(sc, id, n, n1p, sc2, id2, n2p, state, tile_cnt);
@@ -250,7 +256,7 @@ extern "C" cusci_status cusci_topk_workspace(int64_t batch, int64_t K, size_t *b
 extern "C" cusci_status cusci_topk_update(const double *d_scores, const int64_t *d_ids, int64_t n,
                                           int64_t K, double *d_best_scores, int64_t *d_best_ids,
                                           int64_t *d_best_count, void *d_ws, size_t ws_bytes,
-                                          void *stream) {
+                                          int32_t *d_status, void *stream) {
     if (K < 1 || n < 0 || !d_best_scores || !d_best_ids || !d_best_count ||
         (n > 0 && (!d_scores || !d_ids)))
         return fail(CUSCI_ERR_INVALID, "cusci_topk_update: bad argument");
@@ -271,11 +277,11 @@ extern "C" cusci_status cusci_topk_update(const double *d_scores, const int64_t 
     int64_t *cnt = (int64_t *)(ws + sel + 4 * al((size_t)K * 8));  // [0] local, [1] merged
     // level 1: the batch's own best K
     cusci_status rc = select_best(d_scores, d_ids, n, nullptr, nullptr, nullptr, nullptr, 0, K,
-                                  loc_sc, loc_id, cnt, ws, st);
+                                  loc_sc, loc_id, cnt, ws, d_status, st);
     if (rc != CUSCI_OK) return rc;
     // level 2: merged with the running best set
     rc = select_best(d_best_scores, d_best_ids, K, d_best_count, loc_sc, loc_id, cnt, K, K, mrg_sc,
-                     mrg_id, cnt + 1, ws, st);
+                     mrg_id, cnt + 1, ws, nullptr, st);
     if (rc != CUSCI_OK) return rc;
     cudaError_t e = cudaMemcpyAsync(d_best_scores, mrg_sc, (size_t)K * 8, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)

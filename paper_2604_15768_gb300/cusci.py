@@ -56,6 +56,7 @@ _PROTOS = {
     "cusci_dedup_workspace": (_I, [_I64, _I, _I, _I, ctypes.POINTER(_SZ)]),
     "cusci_dedup": (_I, [_P, _I64, _I, _I, _I, _P, _SZ, _P, _P, _I, _P, _P, _P, _P]),
     "cusci_stream_pool_bytes": (_I, [_P, _I64, _I64, _I64, ctypes.POINTER(_SZ)]),
+    "cusci_hash_insert_probe": (_I, [_P, _I64, _I, _P, _I64, _I, _P, _P, _P]),
     "cusci_stream_gen_dedup": (_I, [_P, _P, _I64, _D, _P, _SZ, _I64, _P, _P, _P, _I64, _P, _I64,
                                     _P, _P, _P]),
     "cusci_batch_create": (_I, [_P, _I, _P, _I, ctypes.POINTER(_P)]),
@@ -71,7 +72,7 @@ _PROTOS = {
     "cusci_partition_plan": (_I, [_P, _I, _P, _I, _I, _P, _P, _P]),
     "cusci_reverse_index": (_I, [_P, _I64, _I, _P, _I64, _P, _I, _P, _P]),
     "cusci_topk_workspace": (_I, [_I64, _I64, ctypes.POINTER(_SZ)]),
-    "cusci_topk_update": (_I, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "cusci_topk_update": (_I, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, _P, _P]),
     "cusci_energy_workspace": (_I, [_P, _I64, ctypes.POINTER(_SZ)]),
     "cusci_energy_fwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _SZ, _P, _P]),
     "cusci_energy_bwd": (_I, [_P, _P, _I64, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -279,6 +280,20 @@ def coupled(sys: System, dets: torch.Tensor, eps: float, stream=None):
     return offsets, out_d, out_h, status
 
 
+def hash_insert_probe(keys: torch.Tensor, table: torch.Tensor, spin_limit: int, n_new=None,
+                      status=None, stream=None):
+    """The streaming path's hash-set insert on a caller-built table (see
+    cusci_hash_insert_probe); returns the device counter of new keys."""
+    keys = _dev(keys, torch.int64, "keys")
+    n, W = keys.shape
+    if n_new is None:
+        n_new = torch.zeros(1, dtype=torch.int64, device=keys.device)
+    _check(load().cusci_hash_insert_probe(_ptr(keys), n, W, _ptr(table), table.shape[0],
+                                          int(spin_limit), _ptr(n_new), _ptr(status),
+                                          _stream(stream)), "cusci_hash_insert_probe")
+    return n_new
+
+
 def stream_pool_bytes(sys: System, n_sources: int, batch_entries: int,
                       unique_capacity: int) -> int:
     b = ctypes.c_size_t()
@@ -477,13 +492,16 @@ class TopK:
         self.ws = torch.empty(ws.value, dtype=torch.uint8, device=device)
         self.max_batch = int(max_batch)
 
-    def update(self, scores: torch.Tensor, ids: torch.Tensor, stream=None):
+    def update(self, scores: torch.Tensor, ids: torch.Tensor, status=None, stream=None):
+        """Merge one batch; ``status`` (device int32[1], optional) receives
+        CUSCI_ERR_INVALID if a score is negative or NaN."""
         n = scores.shape[0]
         if n > self.max_batch:
             raise ValueError("batch larger than max_batch")
         _check(load().cusci_topk_update(_ptr(scores), _ptr(ids), n, self.K, _ptr(self.scores),
                                         _ptr(self.ids), _ptr(self.count), _ptr(self.ws),
-                                        self.ws.numel(), _stream(stream)), "cusci_topk_update")
+                                        self.ws.numel(), _ptr(status), _stream(stream)),
+               "cusci_topk_update")
 
     def result(self):
         """(scores, ids) of the best set, best first (host numpy)."""

@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "integrals", "aufbau", "fci_space", "sample_dets", "pack_occ",
-    "words_for", "System", "config_system", "batched_systems",
+    "words_for", "System", "config_system", "batched_systems", "amplitude_mlp",
 ]
 
 
@@ -266,3 +266,18 @@ def batched_systems(n_systems: int = 64, scale: float = 1.0) -> list[System]:
         dets = sample_dets(norb, na, nb, nd, 100000 + s)
         out.append(System(f"sys{s}", norb, na, nb, h1, h2, dets, 1e-8))
     return out
+
+
+def amplitude_mlp(dets: np.ndarray, norb: int, device="cuda"):
+    """The energy workload's network: a 2*norb -> 256 -> 256 -> 1 tanh MLP with
+    FP32 weights from ``torch.manual_seed(0)`` (PyTorch's default init), and its
+    input, the occupation bits (0/1, FP32) of the first word of each
+    determinant.  psi = exp(net(x)) in FP64 is the amplitude of each
+    determinant.  Returns (net, x) on ``device``."""
+    import torch
+    torch.manual_seed(0)
+    net = torch.nn.Sequential(torch.nn.Linear(2 * norb, 256), torch.nn.Tanh(),
+                              torch.nn.Linear(256, 256), torch.nn.Tanh(),
+                              torch.nn.Linear(256, 1)).to(device)
+    bits = ((dets[:, :1] >> np.arange(2 * norb, dtype=np.uint64)) & np.uint64(1)).astype(np.float32)
+    return net, torch.from_numpy(bits).to(device)

@@ -79,3 +79,23 @@ def test_batch_graph_replay_and_autotune(batch):
     b.replay()
     torch.cuda.synchronize()
     check_all(systems, b)
+
+
+def test_batch_replay_unaffected_by_other_eps_on_its_systems(batch):
+    """The batch screens with masks of its own: generating one of its systems
+    at five other eps values (more than the system's mask cache holds) between
+    two graph replays must not change what the replay produces."""
+    systems, b = batch
+    if b.graph is None:
+        b.capture()
+    k = 2
+    s = systems[k]
+    d = cusci.dets_to_device(s.dets)
+    for eps in (1e-3, 1e-4, 1e-5, 1e-6, 1e-7):
+        cusci.coupled(b.systems[k], d, eps)
+    torch.cuda.synchronize()
+    b.out_h.zero_()
+    b.inverse.zero_()
+    b.replay()
+    torch.cuda.synchronize()
+    check_all(systems, b)

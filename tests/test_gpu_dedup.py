@@ -167,3 +167,33 @@ def test_bits_above_declared_width_are_reported():
     cusci.dedup(to_dev(keys), 40, -1, status=st)
     torch.cuda.synchronize()
     assert int(st.item()) == 1
+
+
+def test_sample_sort_wide_and_overflowing_leaves_vs_oracle():
+    """Leaves that leave the shared-memory hash path: (1) full-range 64-bit keys,
+    whose leaves are too wide to pack beside a slot id, and (2) an input whose
+    regularly spaced sample positions all hold one of two heavy keys, so that
+    the splitters equal those two keys and the one leaf between them receives
+    several million distinct keys (far more than its table holds).  Both are
+    sorted in global memory; results must not change."""
+    rng = np.random.default_rng(12)
+    n = 4_600_000
+    wide = rng.integers(0, 2 ** 63, size=n, dtype=np.int64).astype(np.uint64) * np.uint64(2)
+    wide |= rng.integers(0, 2, size=n).astype(np.uint64)
+    wide[::4] = wide[1::4][: wide[::4].size]
+    compare(wide.reshape(-1, 1), 64, -1)
+    # sample positions floor(j * N / NS), NS = 4 samples per leaf, leaves =
+    # 128 per level-1 bucket, level-1 buckets = the power of two covering
+    # N / 2048 / 128 (the plan of the sample-sort path).  Two heavy keys take
+    # turns at those positions, so one leaf spans (2^39, 2^41] with every
+    # distinct key inside: narrow enough for the hash path, too many keys.
+    leaves_wanted = -(-n // 2048)
+    b1 = 1
+    while b1 < -(-leaves_wanted // 128):
+        b1 *= 2
+    ns = min(b1 * 128 * 4, n)
+    keys = np.uint64(1 << 40) + rng.permutation(n).astype(np.uint64) * np.uint64(3)
+    at = (np.arange(ns, dtype=np.int64) * n) // ns
+    keys[at[0::2]] = np.uint64(1 << 39)
+    keys[at[1::2]] = np.uint64(1 << 41)
+    compare(keys.reshape(-1, 1), 42, -1)

@@ -64,3 +64,29 @@ def test_stream_errors_are_reported():
         cusci.stream_gen_dedup(sysd, s.dets[:20], s.eps, 400_000, unique_capacity=1000,
                                host_capacity=1_000_000)
     assert ei.value.status in (2, 4)
+
+
+def test_hash_set_bounded_wait_times_out_and_reports():
+    """The two-word hash insert waits for a claimed slot's second word; with a
+    table whose every slot has its first word set and its second word never
+    written, each wait must give up after the poll limit and report
+    CUSCI_ERR_TIMEOUT (5) through the status word, and the kernel must return.
+    With the second words present the same keys are found and nothing is
+    reported."""
+    keys = torch.tensor([[7, 11], [7, 12], [7, 13]], dtype=torch.int64, device="cuda")
+    slots = 64
+    table = torch.full((slots, 2), -1, dtype=torch.int64, device="cuda")
+    table[:, 0] = 7                      # first word claimed, second word empty
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    n_new = cusci.hash_insert_probe(keys, table, spin_limit=1000, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 5
+    assert int(n_new.item()) == 0
+    # the same probe against a table that holds the keys: found, no error
+    table2 = torch.full((slots, 2), -1, dtype=torch.int64, device="cuda")
+    st2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    n1 = cusci.hash_insert_probe(keys, table2, spin_limit=1000, status=st2)
+    n2 = cusci.hash_insert_probe(keys, table2, spin_limit=1000, status=st2)
+    torch.cuda.synchronize()
+    assert int(st2.item()) == 0
+    assert int(n1.item()) == 3 and int(n2.item()) == 0

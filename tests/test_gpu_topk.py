@@ -40,3 +40,26 @@ def test_topk_fewer_items_than_k():
     tk.update(torch.from_numpy(sc).cuda(), torch.from_numpy(ids).cuda())
     s, i = tk.result()
     assert i.tolist() == [7, 5, 2] and s.tolist() == [0.9, 0.3, 0.1]
+
+
+def test_topk_negative_zero_ranks_as_zero():
+    """-0.0 has its sign bit set; it must still rank below every positive score
+    and tie with +0.0 (then by id)."""
+    tk = cusci.TopK(3, 16)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sc = np.array([-0.0, 0.25, 0.0, 1e-300, -0.0], dtype=np.float64)
+    ids = np.array([4, 9, 1, 6, 0], dtype=np.int64)
+    tk.update(torch.from_numpy(sc).cuda(), torch.from_numpy(ids).cuda(), status=st)
+    s, i = tk.result()
+    assert i.tolist() == [9, 6, 0]
+    assert int(st.item()) == 0
+
+
+def test_topk_negative_or_nan_score_is_reported():
+    for bad in (-0.5, float("nan")):
+        tk = cusci.TopK(2, 16)
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        sc = np.array([0.3, bad, 0.1], dtype=np.float64)
+        tk.update(torch.from_numpy(sc).cuda(), torch.tensor([1, 2, 3], device="cuda"), status=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 1
