@@ -174,14 +174,14 @@ __device__ __forceinline__ void stage(uint64_t *dst, const uint64_t *__restrict_
 // *ones receives the number of set bits among the low n_bits, or -1 if a bit
 // at or above n_bits is set.
 template <int W>
-__device__ __forceinline__ uint64_t sort_key(const uint64_t *__restrict__ k, int mode, int n_bits,
-                                             int kcols, const uint64_t *bt, int *ones) {
+__device__ __forceinline__ uint64_t sort_key_v(const uint64_t (&k)[W], int mode, int n_bits,
+                                               int kcols, const uint64_t *bt, int *ones) {
     uint64_t r = 0;
     int c = 0;
     bool above = false;
 #pragma unroll
     for (int w = 0; w < W; w++) {
-        uint64_t x = __ldg(k + w);
+        uint64_t x = k[w];
         const int hi = n_bits - 64 * w;
         const uint64_t keep = hi >= 64 ? ~0ull : (hi <= 0 ? 0ull : ((1ull << hi) - 1));
         if (x & ~keep) above = true;
@@ -199,6 +199,27 @@ __device__ __forceinline__ uint64_t sort_key(const uint64_t *__restrict__ k, int
     }
     *ones = above ? -1 : c;  // -1: bits above n_bits (invalid key)
     return r;
+}
+
+template <int W>
+__device__ __forceinline__ uint64_t sort_key(const uint64_t *__restrict__ k, int mode, int n_bits,
+                                             int kcols, const uint64_t *bt, int *ones) {
+    uint64_t v[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) v[w] = __ldg(k + w);
+    return sort_key_v<W>(v, mode, n_bits, kcols, bt, ones);
+}
+
+// raw words of the keys i0 + u*stride (u < U), zeros past end
+template <int W, int U>
+__device__ __forceinline__ void load_keys(const uint64_t *__restrict__ keys, int64_t i0,
+                                          int64_t stride, int64_t end, uint64_t (&r)[U][W]) {
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int64_t i = i0 + (int64_t)u * stride;
+#pragma unroll
+        for (int w = 0; w < W; w++) r[u][w] = i < end ? __ldg(keys + i * W + w) : 0ull;
+    }
 }
 
 template <int W>
@@ -355,23 +376,25 @@ __global__ void __launch_bounds__(T)
     int64_t end = beg + per_cta;
     if (end > N) end = N;
     bool bad = false;
+    // the next batch of keys is loaded while the current one is searched
+    uint64_t rn[U1][W];
+    load_keys<W, U1>(keys, beg + threadIdx.x, T, end, rn);
     for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += (int64_t)T * U1) {
-        uint64_t x[U1];
-        int ones[U1];
+        uint64_t r[U1][W];
 #pragma unroll
-        for (int u = 0; u < U1; u++) {
-            const int64_t i = i0 + (int64_t)u * T;
-            x[u] = 0;
-            ones[u] = n_ones;
-            if (i < end) x[u] = sort_key<W>(keys + i * W, mode, n_bits, kcols, bt, &ones[u]);
-        }
+        for (int u = 0; u < U1; u++)
+#pragma unroll
+            for (int w = 0; w < W; w++) r[u][w] = rn[u][w];
+        load_keys<W, U1>(keys, i0 + (int64_t)T * U1, T, end, rn);
 #pragma unroll
         for (int u = 0; u < U1; u++) {
             const int64_t i = i0 + (int64_t)u * T;
             if (i < end) {
-                if ((n_ones >= 0 && ones[u] != n_ones) || ones[u] < 0) bad = true;
-                const int c = cell_of(x[u], kmin, kshift, LG_CELLS1);
-                const int b = count_less_in(S1, T1s[c], T1s[c + 1], x[u]);
+                int ones;
+                const uint64_t x = sort_key_v<W>(r[u], mode, n_bits, kcols, bt, &ones);
+                if ((n_ones >= 0 && ones != n_ones) || ones < 0) bad = true;
+                const int c = cell_of(x, kmin, kshift, LG_CELLS1);
+                const int b = count_less_in(S1, T1s[c], T1s[c + 1], x);
                 bid1[i] = (uint16_t)b;
                 atomicAdd(&h[b], 1u);
             }
@@ -411,45 +434,92 @@ __device__ __forceinline__ uint64_t reserve_slot(unsigned long long *run, uint32
     return base + below;
 }
 
+// exclusive scan of a shared-memory array v[0..n), in place; every thread of
+// the block takes part
+__device__ void block_excl_scan_smem(uint32_t *v, int n, uint32_t *warp_tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int per = (n + T - 1) / T;
+    const int beg = threadIdx.x * per;
+    uint32_t s = 0;
+    for (int k = 0; k < per; k++)
+        if (beg + k < n) s += v[beg + k];
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int w = 0; w < wid; w++) base += warp_tot[w];
+    uint32_t ex = base + inc - s;
+    for (int k = 0; k < per; k++)
+        if (beg + k < n) {
+            const uint32_t c = v[beg + k];
+            v[beg + k] = ex;
+            ex += c;
+        }
+    __syncthreads();
+}
+
+// Level-1 scatter: block c writes its chunk's entries into per-bucket runs of
+// its own region [c*per_cta, ...), slots from plain shared-memory atomics;
+// base1[c][b] receives the run starts (the block-major layout needs only the
+// block's own histogram).  The next batch of keys and bucket ids is loaded
+// while the current one is scattered.
 template <int W>
 __global__ void __launch_bounds__(T)
     scatter1(const uint64_t *__restrict__ keys, int64_t N, int64_t per_cta, int mode, int n_bits,
              int kcols, const uint64_t *__restrict__ bt_g, const uint16_t *__restrict__ bid1,
-             int B1, const int64_t *__restrict__ base1, uint64_t *__restrict__ K1,
-             uint32_t *__restrict__ dest1) {
+             int B1, const uint32_t *__restrict__ H1, int64_t *__restrict__ base1,
+             uint64_t *__restrict__ K1, uint32_t *__restrict__ dest1) {
     extern __shared__ __align__(16) unsigned char sm[];
-    unsigned long long *run = (unsigned long long *)sm;
-    uint64_t *bt = (uint64_t *)(run + B1);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int b = threadIdx.x; b < B1; b += T)
-        run[b] = (unsigned long long)base1[(int64_t)blockIdx.x * B1 + b];
+    uint32_t *run = (uint32_t *)sm;
+    uint64_t *bt = (uint64_t *)(sm + (size_t)MAX_B1 * 4);
+    __shared__ uint32_t warp_tot[WARPS];
+    for (int b = threadIdx.x; b < B1; b += T) run[b] = H1[(int64_t)blockIdx.x * B1 + b];
     if (mode == 1) stage(bt, bt_g, n_bits * kcols);
     __syncthreads();
+    block_excl_scan_smem(run, B1, warp_tot);
     const int64_t beg = (int64_t)blockIdx.x * per_cta;
+    for (int b = threadIdx.x; b < B1; b += T) base1[(int64_t)blockIdx.x * B1 + b] = beg + run[b];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) base1[(int64_t)gridDim.x * B1] = N;
     int64_t end = beg + per_cta;
     if (end > N) end = N;
-    for (int64_t i0 = beg + wid * 32; i0 < end; i0 += (int64_t)WARPS * 32 * U1) {
-        uint64_t x[U1];
+    uint64_t rn[U1][W];
+    uint32_t bn[U1];
+    load_keys<W, U1>(keys, beg + threadIdx.x, T, end, rn);
+#pragma unroll
+    for (int u = 0; u < U1; u++) {
+        const int64_t i = beg + threadIdx.x + (int64_t)u * T;
+        bn[u] = i < end ? bid1[i] : 0u;
+    }
+    for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += (int64_t)T * U1) {
+        uint64_t r[U1][W];
         uint32_t b[U1];
 #pragma unroll
         for (int u = 0; u < U1; u++) {
-            const int64_t i = i0 + (int64_t)u * WARPS * 32 + lane;
-            b[u] = (uint32_t)B1;
-            x[u] = 0;
-            if (i < end) {
-                int ones;
-                b[u] = bid1[i];
-                x[u] = sort_key<W>(keys + i * W, mode, n_bits, kcols, bt, &ones);
-            }
+            b[u] = bn[u];
+#pragma unroll
+            for (int w = 0; w < W; w++) r[u][w] = rn[u][w];
+        }
+        const int64_t i1 = i0 + (int64_t)T * U1;
+        load_keys<W, U1>(keys, i1, T, end, rn);
+#pragma unroll
+        for (int u = 0; u < U1; u++) {
+            const int64_t i = i1 + (int64_t)u * T;
+            bn[u] = i < end ? bid1[i] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < U1; u++) {
-            const int64_t i = i0 + (int64_t)u * WARPS * 32 + lane;
-            const bool valid = i < end;
-            const uint64_t d = reserve_slot(run, b[u], valid, lane);
-            if (valid) {
-                K1[d] = x[u];
-                dest1[i] = (uint32_t)d;
+            const int64_t i = i0 + (int64_t)u * T;
+            if (i < end) {
+                int ones;
+                const uint64_t x = sort_key_v<W>(r[u], mode, n_bits, kcols, bt, &ones);
+                const uint32_t d = (uint32_t)beg + atomicAdd(&run[b[u]], 1u);
+                K1[d] = x;
+                dest1[i] = d;
             }
         }
     }
@@ -883,11 +953,6 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-cusci_status set_smem(const void *fn, size_t bytes) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return e == cudaSuccess ? CUSCI_OK : cuda_fail(e, "dedup: shared-memory attribute");
-}
-
 template <int W>
 cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_t *unique,
                  void *inverse, int index_bytes, int64_t *d_n_unique, int32_t *status,
@@ -923,13 +988,9 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
     launches++;
     // sort the sample with the LSD building blocks
     {
-        static bool attr = false;
         const size_t smem = sizeof(DownSmem<1>);
-        if (!attr) {
-            cusci_status rc = set_smem((const void *)downsweep<1>, smem);
-            if (rc != CUSCI_OK) return rc;
-            attr = true;
-        }
+        cusci_status rc0 = allow_smem((const void *)downsweep<1>, smem, "dedup: smem attribute");
+        if (rc0 != CUSCI_OK) return rc0;
         const int64_t nh = (int64_t)RADIX * p.gs;
         for (int pass = 0; pass < p.s_passes; pass++) {
             upsweep<1><<<p.gs, RT, 0, st>>>(samp, p.NS, pass * RBITS, p.gs_per, shist);
@@ -953,31 +1014,27 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
     // level 1
     const size_t sm_h1 = (size_t)p.B1 * 8 + (p.mode == 1 ? BT_MAX * 8 : 0) + (size_t)p.B1 * 4 +
                          ((size_t)(1 << LG_CELLS1) + 1) * 2;
-    const size_t sm_x1 = (size_t)p.B1 * 8 + BT_MAX * 8;
+    const size_t sm_x1 = (size_t)MAX_B1 * 4 + (p.mode == 1 ? BT_MAX * 8 : 0);
     {
-        static bool attr = false;
-        if (!attr) {
-            cusci_status rc = set_smem((const void *)hist1<W>, (size_t)MAX_B1 * 12 + BT_MAX * 8 +
-                                                   ((size_t)(1 << LG_CELLS1) + 1) * 2);
-            if (rc == CUSCI_OK) rc = set_smem((const void *)scatter1<W>, (size_t)MAX_B1 * 8 + BT_MAX * 8);
-            if (rc == CUSCI_OK) rc = set_smem((const void *)leaf_sort, sizeof(LeafSmem));
-            if (rc != CUSCI_OK) return rc;
-            attr = true;
-        }
+        const char *what = "dedup: smem attribute";
+        cusci_status rc0 = allow_smem((const void *)hist1<W>, (size_t)MAX_B1 * 12 + BT_MAX * 8 +
+                                                                   ((size_t)(1 << LG_CELLS1) + 1) * 2,
+                                      what);
+        if (rc0 == CUSCI_OK)
+            rc0 = allow_smem((const void *)scatter1<W>, (size_t)MAX_B1 * 4 + BT_MAX * 8, what);
+        if (rc0 == CUSCI_OK) rc0 = allow_smem((const void *)leaf_sort, sizeof(LeafSmem), what);
+        if (rc0 != CUSCI_OK) return rc0;
     }
     hist1<W><<<p.G, T, sm_h1, st>>>(keys, p.N, p.per_cta, p.mode, p.n_bits, p.n_ones, p.kcols, bt,
                                     LS, p.B1, p.log2B1, T1, krange, bid1, H1, status);
-    const int64_t nh1 = (int64_t)p.B1 * p.G;
-    widen_u32<<<sms * 2, 256, 0, st>>>(H1, nh1, base1);
-    cusci_status rc = exclusive_scan_i64(base1, nh1, base1, scanws, st);
-    if (rc != CUSCI_OK) return rc;
     scatter1<W><<<p.G, T, sm_x1, st>>>(keys, p.N, p.per_cta, p.mode, p.n_bits, p.kcols, bt, bid1,
-                                       p.B1, base1, K1, dest1);
+                                       p.B1, H1, base1, K1, dest1);
+    cusci_status rc = CUSCI_OK;
     int64_t *kbase = (int64_t *)(ws + p.o_kbase);
     bucket_totals<<<(p.B1 + 255) / 256, 256, 0, st>>>(H1, p.G, p.B1, kbase);
     rc = exclusive_scan_i64(kbase, p.B1, kbase, scanws, st);
     if (rc != CUSCI_OK) return rc;
-    launches += 4;
+    launches += 3;
     // level 2
     level2<<<p.B1, T, 0, st>>>(K1, p.N, base1, H1, p.G, p.B1, kbase, LS, p.NL, bid2, K2, dest2,
                                leafst);
