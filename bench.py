@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -47,7 +48,7 @@ WORKLOADS = {
              "in HBM (no streaming)",
 }
 
-TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 116.42, "cusci_gen_coupled (fill_kernel)": 15.93}
+TRAFFIC_B_PER_ENTRY = {"cusci_dedup": None, "cusci_gen_coupled (fill_kernel)": 15.93}
 UNIT = "entries/s"
 
 
@@ -70,11 +71,11 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="cusci_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
@@ -115,6 +116,10 @@ class ClockSampler:
         if sm:
             out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), samples=len(sm))
         out["reasons"] = sorted(reasons)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         return out
 
 
@@ -427,50 +432,50 @@ def run_ours(args):
 
 
 def run_e2e(args, s, sysd, dev):
-    """Same metric through the public API with host buffers: pinned host sources
-    copied in, count/scan/fill/dedup, the step's result (total and distinct
-    counts) read back, every step."""
+    """Same metric through the public API with host buffers: every step copies
+    the sources in from pinned host memory, runs count/scan/fill/dedup, and
+    copies the step's result -- the sorted distinct targets and the reverse
+    index of every coupled entry -- back to pinned host memory."""
     import torch
 
     from paper_2604_15768_gb300 import cusci
     host = torch.from_numpy(np.ascontiguousarray(s.dets).view(np.int64)).pin_memory()
     n_bits, n_ones = 2 * s.norb, s.n_alpha + s.n_beta
-    res = torch.empty(2, dtype=torch.int64).pin_memory()
-    times, total = [], 0
+    W = s.dets.shape[1]
+    # sizes of the result (deterministic: the same every step)
+    d = host.to(dev)
+    off, od, oh, st = cusci.coupled(sysd, d, s.eps)
+    u, inv, nu = cusci.dedup(od, n_bits, n_ones)
+    total, n_unique = int(od.shape[0]), int(nu)
+    del d, off, od, oh, st, u, inv
+    torch.cuda.empty_cache()
+    h_unique = torch.empty((n_unique, W), dtype=torch.int64).pin_memory()
+    h_inverse = torch.empty(total, dtype=torch.int32 if total < 2 ** 31 else torch.int64).pin_memory()
+    times = []
 
     def one():
         d = host.to(dev, non_blocking=True)
         off, od, oh, st = cusci.coupled(sysd, d, s.eps)
         u, inv, d_nu = cusci.dedup(od, n_bits, n_ones, sync=False)
-        out = torch.stack([off[-1], d_nu[0]])
-        res.copy_(out, non_blocking=True)
+        h_unique.copy_(u[:n_unique], non_blocking=True)
+        h_inverse.copy_(inv, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-        return int(res[0])
+        return int(od.shape[0])
 
     for _ in range(2):
         one()
     for _ in range(max(2, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        total = one()
+        got = one()
         times.append(time.perf_counter() - t0)
+        assert got == total
     t = float(np.mean(times))
+    d2h = int(h_unique.numel() * 8 + h_inverse.numel() * h_inverse.element_size())
     return {"value": total / t, "unit": UNIT, "h2d_bytes_per_step": int(host.numel() * 8),
-            "d2h_bytes_per_step": 16, "ms_per_step": t * 1e3,
-            "api": "cusci.coupled + cusci.dedup (host-pinned sources in, totals out)"}
-
-
-def mlp_psi(S_np, norb, dev):
-    """psi = exp(logamp) from a seeded MLP (occupation bits -> 256 -> 256 -> 1,
-    tanh, FP32 weights, FP64 output)."""
-    import torch
-    torch.manual_seed(0)
-    net = torch.nn.Sequential(torch.nn.Linear(2 * norb, 256), torch.nn.Tanh(),
-                              torch.nn.Linear(256, 256), torch.nn.Tanh(),
-                              torch.nn.Linear(256, 1)).to(dev)
-    bits = ((S_np[:, :1] >> np.arange(2 * norb, dtype=np.uint64)) & np.uint64(1)).astype(np.float32)
-    x = torch.from_numpy(bits).to(dev)
-    return net, x
+            "d2h_bytes_per_step": d2h, "ms_per_step": t * 1e3,
+            "api": "cusci.coupled + cusci.dedup (host-pinned sources in; sorted distinct set "
+                   "and reverse index out to pinned host memory)"}
 
 
 def run_energy(args, dev):
@@ -480,7 +485,7 @@ def run_energy(args, dev):
     s = synth.config_system("energy", n_dets=args.energy_sources)
     sysd = cusci.System.of(s)
     dS = cusci.dets_to_device(s.dets, dev)
-    net, x = mlp_psi(s.dets, s.norb, dev)
+    net, x = synth.amplitude_mlp(s.dets, s.norb, dev)
 
     def fwd_bwd():
         psi = torch.exp(net(x).squeeze(-1).double())
@@ -515,18 +520,27 @@ def run_energy(args, dev):
 def run_stream(args, dev):
     """Large two-word system (120 spin orbitals, 10a+10b, 20k sources, eps 1e-6)
     through mini-batches of a bounded pool, coupled lists offloaded to pinned
-    host memory."""
+    host memory.  The distinct-set capacity is the measured distinct count plus
+    10% (the pool then holds the hash set of the distinct keys, the two batch
+    buffers and the per-source arrays); a plain pinned device-to-host copy of
+    the same bytes is timed beside it, and the peak pool use is reported
+    against the batch size with and without the offload (Sec. 5.6)."""
     import torch
 
     from paper_2604_15768_gb300 import cusci, synth
     s = synth.config_system("large", n_dets=args.stream_sources)
     sysd = cusci.System.of(s)
     batch = args.stream_batch
-    ucap = args.stream_unique_cap
-    # host capacity from the counts (one untimed count pass)
+    # host capacity from the counts and distinct capacity from one untimed run
     d = cusci.dets_to_device(s.dets, dev)
     total = int(cusci.count_coupled(sysd, d, s.eps).sum().item())
     del d
+    torch.cuda.empty_cache()
+    probe = cusci.stream_gen_dedup(sysd, s.dets, s.eps, batch, total, host_capacity=total)
+    n_distinct = int(probe[3].shape[0])
+    del probe
+    torch.cuda.empty_cache()
+    ucap = int(n_distinct * 1.1) + 1024 if args.stream_unique_cap <= 0 else args.stream_unique_cap
     hcap = total
     buffers = cusci.stream_buffers(sysd, s.dets, batch, ucap, hcap)
     res = None
@@ -539,6 +553,35 @@ def run_stream(args, dev):
         times.append(time.perf_counter() - t0)
     off, hd, hh, uniq, st = res
     t = min(times[1:]) if len(times) > 1 else times[0]
+    # yardstick: one plain pinned copy of the same byte count
+    nbytes = int(st["d2h_bytes"])
+    src = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    dst = hd.view(torch.uint8).reshape(-1)[:nbytes] if hd.numel() * 8 >= nbytes else \
+        torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    ys = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        ys.append(time.perf_counter() - t0)
+    plain_gbs = nbytes / min(ys) / 1e9
+    del src
+    # peak pool use against the batch size, with and without the offload
+    curve = []
+    for be in (batch // 4, batch, batch * 4):
+        for offload in (True, False):
+            bufs = cusci.stream_buffers(sysd, s.dets, be, ucap, 0)
+            bufs["hd"], bufs["hh"] = buffers["hd"], buffers["hh"]  # pinned sinks reused
+            r = cusci.stream_gen_dedup(sysd, s.dets, s.eps, be, ucap, offload=offload,
+                                       buffers=bufs)
+            del bufs
+            curve.append({"batch_entries": be, "offload": offload,
+                          "pool_bytes": int(r[4]["pool_bytes"]),
+                          "pool_peak_bytes": int(r[4]["pool_peak"]),
+                          "batches": int(r[4]["batches"])})
+            del r
+            torch.cuda.empty_cache()
     # Stage-3 reverse index of the host-resident coupled set against the device
     # distinct set, streamed back in batches
     total_e = st["total"]
@@ -567,7 +610,8 @@ def run_stream(args, dev):
             "batch_entries": batch, "pool_bytes": st["pool_bytes"],
             "pool_peak_bytes": st["pool_peak"], "batch_region_bytes": 2 * batch * 24,
             "coupled_set_bytes": st["total"] * 24, "d2h_bytes": st["d2h_bytes"],
-            "d2h_gbs": st["d2h_bytes"] / t / 1e9,
+            "d2h_gbs": st["d2h_bytes"] / t / 1e9, "plain_pinned_d2h_gbs": plain_gbs,
+            "unique_capacity": ucap, "peak_vs_batch": curve,
             "reverse_index": rev,
             "workload": f"large: 120 spin orbitals (2 words), 10a+10b, {s.dets.shape[0]} sources, "
                         "eps 1e-6; host sources in, host coupled lists + device distinct set out; "
@@ -575,45 +619,79 @@ def run_stream(args, dev):
 
 
 def run_batched(args, dev):
-    """64 independent systems of uneven size in one persistent launch per pass,
-    per-system de-duplication, the whole sequence replayed from a CUDA graph."""
+    """64 independent systems of uneven size (the batched workload; at
+    --batch-scale 1, 1k-50k sources per system).  Systems are taken in order in
+    waves of at most --batch-wave-entries coupled entries (the whole workload,
+    ~6.4e9 entries, does not fit the device at once); every wave is one Batch:
+    one persistent count launch, one persistent fill launch and one batched
+    de-duplication of all its systems, autotuned (work-item size and grid) and
+    replayed from a CUDA graph.  The time is the sum of the waves' replays."""
     import torch
 
     from paper_2604_15768_gb300 import cusci, synth
     t0 = time.perf_counter()
     systems = synth.batched_systems(64, scale=args.batch_scale)
     t_synth = time.perf_counter() - t0
-    b = cusci.Batch(systems, [x.dets for x in systems], 1e-8, chunk=8)
-    b.plan()
-    chunk, _ = b.autotune()
-    b.capture()
-    for _ in range(2):
-        b.replay()
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(3):
-        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        b.replay()
-        z.record()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(z))
-    ms = float(np.median(ts))
+    # exact entries of every system (one count pass each) to form the waves
+    sizes = []
+    for x in systems:
+        sysd = cusci.System.of(x)
+        sizes.append(int(cusci.count_coupled(sysd, cusci.dets_to_device(x.dets, dev),
+                                             x.eps).sum().item()))
+        del sysd
+    waves, cur, acc = [], [], 0
+    for k, m in enumerate(sizes):
+        if cur and acc + m > args.batch_wave_entries:
+            waves.append(cur)
+            cur, acc = [], 0
+        cur.append(k)
+        acc += m
+    if cur:
+        waves.append(cur)
     hbm_peak, _ = _peaks()
-    nus = b.n_unique.cpu().numpy()
-    alg = 0
-    for k, x in enumerate(systems):
-        m = int(b.entry_begin[k + 1] - b.entry_begin[k])
-        wbytes = 8 * x.W
-        alg += m * (wbytes + 8) + m * (wbytes + 4) + int(nus[k]) * wbytes
-    return {"entries_per_s": b.total / (ms * 1e-3), "ms": ms, "entries": b.total,
-            "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
-            "frac_of_hbm": alg / (ms * 1e-3) / 1e9 / hbm_peak,
-            "systems": len(systems), "sources": int(b.n), "chunk": int(chunk),
-            "unique_total": int(b.n_unique.sum().item()), "synth_s": t_synth,
+    total_ms, total_entries, alg, uniq_total, launches, tuned = 0.0, 0, 0, 0, 0, []
+    for wv in waves:
+        ws_ = [systems[k] for k in wv]
+        b = cusci.Batch(ws_, [x.dets for x in ws_], 1e-8, chunk=8)
+        b.plan()
+        (chunk, grid), _ = b.autotune(candidates=(1, 4, 16, 64), grids=(4, 8, 16), reps=1)
+        b.capture()
+        for _ in range(2):
+            b.replay()
+        torch.cuda.synchronize()
+        l0 = cusci.kernel_launches()
+        ts = []
+        for _ in range(3):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            b.replay()
+            z.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(z))
+        total_ms += float(np.median(ts))
+        total_entries += b.total
+        nus = b.n_unique.cpu().numpy()
+        assert int(b.status.item()) == 0
+        for j, x in enumerate(ws_):
+            m = int(b.entry_begin[j + 1] - b.entry_begin[j])
+            wbytes = 8 * x.W
+            alg += m * (wbytes + 8) + m * (wbytes + 4) + int(nus[j]) * wbytes
+        uniq_total += int(nus.sum())
+        tuned.append({"systems": len(wv), "entries": b.total, "chunk": int(chunk),
+                      "blocks_per_sm": int(grid), "ms": float(np.median(ts))})
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+    return {"entries_per_s": total_entries / (total_ms * 1e-3), "ms": total_ms,
+            "entries": total_entries, "algorithmic_bytes": alg,
+            "achieved_gbs": alg / (total_ms * 1e-3) / 1e9,
+            "frac_of_hbm": alg / (total_ms * 1e-3) / 1e9 / hbm_peak,
+            "systems": len(systems), "sources": int(sum(x.dets.shape[0] for x in systems)),
+            "waves": tuned, "unique_total": uniq_total, "synth_s": t_synth,
             "workload": f"64 systems, norb 10..50, 4..16 electrons, sources "
-                        f"floor(logU(1e3,5e4) x {args.batch_scale}), eps 1e-8, graph replay "
-                        "of count+scan+fill+per-system dedup"}
+                        f"floor(logU(1e3,5e4) x {args.batch_scale}), eps 1e-8; waves of at most "
+                        f"{args.batch_wave_entries:.3g} entries, each a graph replay of "
+                        "count+scan+fill+batched dedup"}
 
 
 REF_SOURCES = {"mid": 2000, "tiny": None, "large": 60}
@@ -639,6 +717,39 @@ def run_cpu_baseline(args):
                       f"(count+gen+dedup, {int(off[-1])} entries, {t:.1f} s)"}
 
 
+def run_profile(args):
+    """Profiling driver (for ncu): count -> scan -> fill -> dedup of the first
+    ``--profile-sources`` sources of the workload through the public API, the
+    warm-up steps and then ``--steps`` steps, with no extra legs.  Prints one
+    JSON line with the sizes and CUDA-event times; not a benchmark line."""
+    import torch
+
+    from paper_2604_15768_gb300 import cusci, synth
+
+    torch.cuda.set_device(0)
+    s = synth.config_system(args.workload, n_dets=args.profile_sources)
+    sysd = cusci.System.of(s)
+    n, W = s.dets.shape
+    d_src = cusci.dets_to_device(s.dets)
+    n_bits, n_ones = 2 * s.norb, s.n_alpha + s.n_beta
+    times = []
+    for it in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        off, od, oh, st = cusci.coupled(sysd, d_src, s.eps)
+        u, inv, nu = cusci.dedup(od, n_bits, n_ones, sync=False)
+        b.record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            times.append(a.elapsed_time(b))
+        total = od.shape[0]
+        n_unique = int(nu.item())
+        del off, od, oh, st, u, inv, nu
+    print(json.dumps({"profile": WORKLOADS[args.workload].format(n=n), "entries": total,
+                      "unique": n_unique, "ms": times}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -660,9 +771,15 @@ def main(argv=None):
     ap.add_argument("--no-ranks", dest="ranks", action="store_false")
     ap.add_argument("--stream-sources", type=int, default=20_000)
     ap.add_argument("--stream-batch", type=int, default=16_000_000)
-    ap.add_argument("--stream-unique-cap", type=int, default=400_000_000)
-    ap.add_argument("--batch-scale", type=float, default=0.25)
+    ap.add_argument("--stream-unique-cap", type=int, default=0,
+                    help="distinct-set capacity of the streaming leg (0: measured + 10%%)")
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--batch-wave-entries", type=float, default=1.2e9)
+    ap.add_argument("--profile-sources", type=int, default=None,
+                    help="profiling driver: count/scan/fill/dedup of this many sources only")
     args = ap.parse_args(argv)
+    if args.profile_sources:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -210,9 +210,12 @@ cusci_status cusci_local_energy_fwd(const int64_t *d_offsets, int64_t n, const d
                                     double *d_norm2, void *d_ws, size_t ws_bytes, void *stream);
 /* Adjoint: d_grad_u[u] = g ( sum_{e: inverse[e]=u} psi_{i(e)} H_e
  *   + sum_{rows i whose source is u} (y_i - 2 E psi_i) ) / norm2, g = *d_grad_out
- * (NULL: 1).  d_y from the forward call, or NULL to recompute (then the
- * workspace is needed).  The scatter-add uses FP64 atomics: results agree with
- * any other summation order to rounding, not bit for bit. */
+ * (NULL: 1).  d_y from the forward call, or NULL to recompute it.  The
+ * scatter-add runs in 128-bit fixed point (integer atomics), so the gradient
+ * is bit-reproducible run to run and exact up to a 2^-64 truncation per term.
+ * Workspace: cusci_local_energy_bwd_workspace(n, n_unique) bytes, 256-byte
+ * aligned (16 bytes per distinct configuration plus the rows' scratch). */
+cusci_status cusci_local_energy_bwd_workspace(int64_t n, int64_t n_unique, size_t *bytes);
 cusci_status cusci_local_energy_bwd(const int64_t *d_offsets, int64_t n, const double *d_h,
                                     const void *d_inverse, int index_bytes,
                                     const double *d_psi_u, int64_t n_unique, const double *d_y,
@@ -340,6 +343,30 @@ cusci_status cusci_batch_count(cusci_batch *batch, const uint64_t *d_dets, doubl
 cusci_status cusci_batch_gen(cusci_batch *batch, const uint64_t *d_dets, double eps,
                              const int64_t *d_offsets, uint64_t *d_out_dets, double *d_out_h,
                              int32_t *d_status, void *stream);
+/* Blocks per SM of the persistent count / fill grid (1..32; default 8), the
+ * second knob of the batch's autotuner beside the work-item size. */
+cusci_status cusci_batch_set_grid(cusci_batch *batch, int blocks_per_sm);
+/* De-duplication of every system's targets in one pass (the in-batch
+ * de-duplication of Sec. 4.1, per system, over the whole batch): target e of
+ * system k becomes base_k + its combinatorial rank among the C(M_k, n_k)
+ * determinants of system k -- an order-preserving 64-bit key whose ranges are
+ * disjoint and in system order -- so one sort yields all systems' sorted
+ * distinct sets.  d_offsets / d_targets as written by cusci_batch_gen (total
+ * entries).  Outputs per system k, whose entries are
+ * [d_offsets[first source of k], d_offsets[first source of k+1]): its sorted
+ * distinct targets at the same positions of d_unique (device [total][2]), the
+ * id of every entry's target within them in d_inverse (device int32[total]),
+ * their number in d_n_unique[k] (device int64[n_systems]).  d_status (device
+ * int32, nullable): CUSCI_ERR_INVALID if a target has the wrong electron count
+ * or bits above M.  Asynchronous; the number of launches does not depend on
+ * the number of systems.  Errors: CUSCI_ERR_UNSUPPORTED if the systems' rank
+ * spaces sum to 2^64 or more, or total >= 2^31; CUSCI_ERR_OOM (workspace).
+ * Workspace: cusci_batch_dedup_workspace(batch, total) bytes, 256-byte aligned. */
+cusci_status cusci_batch_dedup_workspace(const cusci_batch *batch, int64_t total, size_t *bytes);
+cusci_status cusci_batch_dedup(cusci_batch *batch, const int64_t *d_offsets,
+                               const uint64_t *d_targets, int64_t total, void *d_ws,
+                               size_t ws_bytes, uint64_t *d_unique, int32_t *d_inverse,
+                               int64_t *d_n_unique, int32_t *d_status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,7 @@
 // captured in a CUDA graph and replayed.
 
 #include <algorithm>
+#include <mutex>
 #include <stdlib.h>
 #include <string.h>
 #include <vector>
@@ -30,7 +31,17 @@ struct cusci_batch {
     int4 *d_items;                   // device work list: (system, first, count, unused)
     int n_items;
     int chunk;
+    int blocks_per_sm;               // persistent grid: blocks per SM of the count/fill launches
     unsigned int *d_counter;         // device [2]: work cursor of the count and fill launches
+    // batched de-duplication: per system its spin-orbital count M and electron
+    // count (device int2[n_sys]) and the base of its rank range in the joint
+    // key space (device uint64[n_sys + 1]; base[n_sys] = size of that space)
+    int2 *d_sysinfo;
+    uint64_t *d_base;
+    int64_t *d_src_begin;            // device copy of src_begin (first dedup call)
+    bool d_src_begin_ready;
+    uint64_t space;                  // sum of C(M_k, n_k); 0 if it does not fit 64 bits
+    int key_bits;
 };
 
 namespace cusci {
@@ -175,7 +186,7 @@ cusci_status launch(cusci_batch *b, bool fill, const uint64_t *d_dets, double ep
     unsigned int *cur = b->d_counter + (fill ? 1 : 0);
     cudaError_t e = cudaMemsetAsync(cur, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return cuda_fail(e, "batch: cursor");
-    const int grid = sm_count() * 8;
+    const int grid = sm_count() * b->blocks_per_sm;
     if (fill)
         batch_kernel<true><<<grid, 32 * BW, 0, st>>>(b->d_views, b->d_items, b->n_items, cur,
                                                      d_dets, eps, d_counts, d_offsets, d_out, d_h,
@@ -187,6 +198,152 @@ cusci_status launch(cusci_batch *b, bool fill, const uint64_t *d_dets, double ep
     CUSCI_LAUNCHED(1, "batch kernel");
     return CUSCI_OK;
 }
+
+
+// ---------------------------------------------------------------- batched de-duplication
+// Every target of system k is mapped to base_k + its combinatorial rank among
+// the C(M_k, n_k) determinants of that system (rank = sum over the set bits,
+// in increasing position p with running count c = 1, 2, ..., of C(p, c)); the
+// map is order preserving within a system and the systems' ranges are
+// disjoint and ordered, so one de-duplication of these 64-bit keys yields
+// every system's sorted distinct set, contiguous and in system order.
+
+__device__ uint64_t g_bbinom[128 * 65];  // C(m, c) for m < 128, c <= 64 (saturated)
+std::mutex g_bbinom_mu;
+bool g_bbinom_ready[64] = {false};
+
+unsigned __int128 binom_u128(int m, int k) {
+    if (k < 0 || k > m) return 0;
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; i++) r = r * (unsigned)(m - k + i) / (unsigned)i;
+    return r;
+}
+
+cusci_status ensure_bbinom() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return fail(CUSCI_ERR_INVALID, "batch: device id out of range");
+    std::lock_guard<std::mutex> lk(g_bbinom_mu);
+    if (g_bbinom_ready[dev]) return CUSCI_OK;
+    static uint64_t host[128 * 65];
+    for (int m = 0; m < 128; m++)
+        for (int c = 0; c <= 64; c++) {
+            const unsigned __int128 v = binom_u128(m, c);
+            host[m * 65 + c] = v > (unsigned __int128)~0ull ? ~0ull : (uint64_t)v;
+        }
+    cudaError_t e = cudaMemcpyToSymbol(g_bbinom, host, sizeof(host));
+    if (e != cudaSuccess) return cuda_fail(e, "batch: binomial table");
+    g_bbinom_ready[dev] = true;
+    return CUSCI_OK;
+}
+
+// largest k with v[k] <= x over v[0..n] (v ascending, v[0] <= x)
+__device__ __forceinline__ int seg_of(const int64_t *v, int n, int64_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (v[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// entry begins of the systems: ebeg[k] = offsets[src_begin[k]]
+__global__ void bd_ebeg(const int64_t *__restrict__ offsets, const int64_t *__restrict__ src_begin,
+                        int n_sys, int64_t *__restrict__ ebeg) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= n_sys) ebeg[k] = offsets[src_begin[k]];
+}
+
+__global__ void bd_keys(const uint64_t *__restrict__ tgt, int64_t total,
+                        const int64_t *__restrict__ ebeg, int n_sys,
+                        const int2 *__restrict__ info, const uint64_t *__restrict__ base,
+                        uint64_t *__restrict__ keys, int32_t *__restrict__ status) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = seg_of(ebeg, n_sys + 1, e);
+        const int2 in = info[k];
+        uint64_t r = 0;
+        int c = 0;
+        bool bad = false;
+#pragma unroll
+        for (int w = 0; w < 2; w++) {
+            uint64_t x = tgt[2 * e + w];
+            const int hi = in.x - 64 * w;
+            const uint64_t keep = hi >= 64 ? ~0ull : (hi <= 0 ? 0ull : ((1ull << hi) - 1));
+            if (x & ~keep) bad = true;
+            for (x &= keep; x; x &= x - 1) {
+                const int pos = 64 * w + __ffsll((long long)x) - 1;
+                c++;
+                if (c <= 64) r += g_bbinom[pos * 65 + c];
+            }
+        }
+        if ((bad || c != in.y) && status) *status = CUSCI_ERR_INVALID;
+        keys[e] = base[k] + r;
+    }
+}
+
+// first distinct index of every system: ub[k] = number of distinct keys < base[k]
+__global__ void bd_bounds(const uint64_t *__restrict__ uniq, const int64_t *__restrict__ d_nu,
+                          const uint64_t *__restrict__ base, int n_sys, int64_t *__restrict__ ub,
+                          int64_t *__restrict__ n_unique) {
+    const int k = threadIdx.x;  // one block
+    const int64_t nu = *d_nu;
+    if (k <= n_sys) {
+        int64_t lo = 0, hi = nu;
+        if (k == n_sys) {
+            lo = nu;
+        } else {
+            const uint64_t x = base[k];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (uniq[mid] < x) lo = mid + 1;
+                else hi = mid;
+            }
+        }
+        ub[k] = lo;
+    }
+    __syncthreads();
+    if (k < n_sys) n_unique[k] = ub[k + 1] - ub[k];
+}
+
+// distinct keys back to determinants, at each system's entry range
+__global__ void bd_unrank(const uint64_t *__restrict__ uniq, const int64_t *__restrict__ d_nu,
+                          const int64_t *__restrict__ ub, const int64_t *__restrict__ ebeg,
+                          int n_sys, const int2 *__restrict__ info,
+                          const uint64_t *__restrict__ base, uint64_t *__restrict__ out) {
+    const int64_t nu = *d_nu;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nu;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int k = seg_of(ub, n_sys + 1, j);
+        const int2 in = info[k];
+        uint64_t v = uniq[j] - base[k];
+        uint64_t d[2] = {0ull, 0ull};
+        int p = in.x - 1;
+        for (int c = in.y; c >= 1; c--) {
+            while (p >= c && g_bbinom[p * 65 + c] > v) p--;
+            if (p >= c) v -= g_bbinom[p * 65 + c];
+            if (p >= 0) d[p >> 6] |= 1ull << (p & 63);
+            p--;
+        }
+        const int64_t at = ebeg[k] + (j - ub[k]);
+        out[2 * at] = d[0];
+        out[2 * at + 1] = d[1];
+    }
+}
+
+// global distinct ids to ids within each system
+__global__ void bd_localize(int32_t *__restrict__ inv, int64_t total,
+                            const int64_t *__restrict__ ebeg, int n_sys,
+                            const int64_t *__restrict__ ub) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = seg_of(ebeg, n_sys + 1, e);
+        inv[e] = (int32_t)(inv[e] - ub[k]);
+    }
+}
+
+size_t bd_al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 }  // namespace cusci
@@ -219,9 +376,35 @@ extern "C" cusci_status cusci_batch_create(const cusci_system *const *systems, i
     b->d_views = NULL;
     b->d_items = NULL;
     b->d_counter = NULL;
+    b->d_sysinfo = NULL;
+    b->d_base = NULL;
+    b->d_src_begin = NULL;
+    b->d_src_begin_ready = false;
+    b->blocks_per_sm = 8;
     b->masks.assign(n_systems, NULL);
+    // joint key space of the batched de-duplication
+    std::vector<int2> info(n_systems);
+    std::vector<uint64_t> base(n_systems + 1, 0);
+    bool fits = true;
+    for (int k = 0; k < n_systems; k++) {
+        info[k] = make_int2(systems[k]->M, systems[k]->n_alpha + systems[k]->n_beta);
+        const unsigned __int128 c = binom_u128(info[k].x, info[k].y);
+        const unsigned __int128 nb = (unsigned __int128)base[k] + c;
+        if (c > (unsigned __int128)~0ull || nb > (unsigned __int128)~0ull) fits = false;
+        base[k + 1] = fits ? (uint64_t)nb : 0ull;
+    }
+    b->space = fits ? base[n_systems] : 0ull;
+    b->key_bits = 1;
+    while (b->key_bits < 64 && (b->space - 1) >> b->key_bits) b->key_bits++;
     cudaError_t e = cudaMalloc(&b->d_views, sizeof(SysView) * n_systems);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sysinfo, sizeof(int2) * n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_base, sizeof(uint64_t) * (n_systems + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_sysinfo, info.data(), sizeof(int2) * n_systems, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_base, base.data(), sizeof(uint64_t) * (n_systems + 1),
+                       cudaMemcpyHostToDevice);
     for (int k = 0; k < n_systems && e == cudaSuccess; k++)
         e = cudaMalloc(&b->masks[k], mask_words(systems[k]) * sizeof(uint64_t));
     if (e != cudaSuccess) {
@@ -242,6 +425,9 @@ extern "C" void cusci_batch_destroy(cusci_batch *b) {
     cudaFree(b->d_views);
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
+    cudaFree(b->d_sysinfo);
+    cudaFree(b->d_base);
+    cudaFree(b->d_src_begin);
     for (uint64_t *m : b->masks) cudaFree(m);
     delete b;
 }
@@ -272,4 +458,81 @@ extern "C" cusci_status cusci_batch_gen(cusci_batch *b, const uint64_t *d_dets, 
         return fail(CUSCI_ERR_INVALID, "cusci_batch_gen: outputs misaligned");
     return launch(b, true, d_dets, eps, NULL, d_offsets, d_out_dets, d_out_h, d_status,
                   (cudaStream_t)stream);
+}
+
+extern "C" cusci_status cusci_batch_set_grid(cusci_batch *b, int blocks_per_sm) {
+    if (!b || blocks_per_sm < 1 || blocks_per_sm > 32)
+        return fail(CUSCI_ERR_INVALID, "cusci_batch_set_grid: bad argument");
+    b->blocks_per_sm = blocks_per_sm;
+    return CUSCI_OK;
+}
+
+extern "C" cusci_status cusci_batch_dedup_workspace(const cusci_batch *b, int64_t total,
+                                                    size_t *bytes) {
+    if (!b || !bytes || total < 0)
+        return fail(CUSCI_ERR_INVALID, "cusci_batch_dedup_workspace: bad argument");
+    if (b->space == 0)
+        return fail(CUSCI_ERR_UNSUPPORTED, "cusci_batch_dedup: joint key space exceeds 64 bits");
+    size_t inner = 0;
+    cusci_status rc = cusci_dedup_workspace(total > 0 ? total : 1, 1, b->key_bits, -1, &inner);
+    if (rc != CUSCI_OK) return rc;
+    const size_t t = (size_t)(total > 0 ? total : 1);
+    *bytes = bd_al(t * 8) * 2 + bd_al(((size_t)b->n_sys + 1) * 8) * 2 + bd_al(8) + bd_al(inner);
+    return CUSCI_OK;
+}
+
+extern "C" cusci_status cusci_batch_dedup(cusci_batch *b, const int64_t *d_offsets,
+                                          const uint64_t *d_targets, int64_t total, void *d_ws,
+                                          size_t ws_bytes, uint64_t *d_unique, int32_t *d_inverse,
+                                          int64_t *d_n_unique, int32_t *d_status, void *stream) {
+    if (!b || !d_offsets || (total > 0 && (!d_targets || !d_unique || !d_inverse)) || !d_n_unique)
+        return fail(CUSCI_ERR_INVALID, "cusci_batch_dedup: bad argument");
+    if (total >= ((int64_t)1 << 31))
+        return fail(CUSCI_ERR_UNSUPPORTED, "cusci_batch_dedup: int32 ids need fewer than 2^31 entries");
+    size_t need = 0;
+    cusci_status rc = cusci_batch_dedup_workspace(b, total, &need);
+    if (rc != CUSCI_OK) return rc;
+    if (!d_ws || ws_bytes < need || ((uintptr_t)d_ws & 255u))
+        return fail(CUSCI_ERR_OOM, "cusci_batch_dedup: workspace %zu < %zu bytes (or misaligned)",
+                    ws_bytes, need);
+    rc = ensure_bbinom();
+    if (rc != CUSCI_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ns = b->n_sys;
+    if (total == 0) {
+        cudaError_t e = cudaMemsetAsync(d_n_unique, 0, sizeof(int64_t) * ns, st);
+        return e == cudaSuccess ? CUSCI_OK : cuda_fail(e, "cusci_batch_dedup: memset");
+    }
+    unsigned char *w = (unsigned char *)d_ws;
+    const size_t t = (size_t)total;
+    uint64_t *keys = (uint64_t *)w; w += bd_al(t * 8);
+    uint64_t *uniq = (uint64_t *)w; w += bd_al(t * 8);
+    int64_t *ebeg = (int64_t *)w; w += bd_al(((size_t)ns + 1) * 8);
+    int64_t *ub = (int64_t *)w; w += bd_al(((size_t)ns + 1) * 8);
+    int64_t *d_nu = (int64_t *)w; w += bd_al(8);
+    void *inner = w;
+    const size_t inner_bytes = ws_bytes - (size_t)(w - (unsigned char *)d_ws);
+    // source begins of the systems, on the device once
+    if (!b->d_src_begin_ready) {
+        cudaError_t e = cudaMalloc(&b->d_src_begin, sizeof(int64_t) * (ns + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_src_begin, b->src_begin.data(), sizeof(int64_t) * (ns + 1),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cusci_batch_dedup: source begins");
+        b->d_src_begin_ready = true;
+    }
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
+    bd_ebeg<<<1, 128 * ((ns + 128) / 128), 0, st>>>(d_offsets, b->d_src_begin, ns, ebeg);
+    bd_keys<<<blocks, 256, 0, st>>>(d_targets, total, ebeg, ns, b->d_sysinfo, b->d_base, keys,
+                                    d_status);
+    CUSCI_LAUNCHED(2, "batched dedup keys");
+    rc = cusci_dedup(keys, total, 1, b->key_bits, -1, inner, inner_bytes, uniq, d_inverse, 4, d_nu,
+                     NULL, d_status, stream);
+    if (rc != CUSCI_OK) return rc;
+    bd_bounds<<<1, 128 * ((ns + 128) / 128), 0, st>>>(uniq, d_nu, b->d_base, ns, ub, d_n_unique);
+    bd_unrank<<<blocks, 256, 0, st>>>(uniq, d_nu, ub, ebeg, ns, b->d_sysinfo, b->d_base, d_unique);
+    bd_localize<<<blocks, 256, 0, st>>>(d_inverse, total, ebeg, ns, ub);
+    CUSCI_LAUNCHED(3, "batched dedup split");
+    return CUSCI_OK;
 }

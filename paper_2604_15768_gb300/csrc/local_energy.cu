@@ -8,8 +8,13 @@
 // reduction of the row terms (deterministic).  Adjoint:
 //   dE/dpsi_u[u] = ( sum_{e: inverse[e]=u} psi_{i(e)} H_e
 //                    + sum_{i: source of i is u} (y_i - 2 E psi_i) ) / sum psi_i^2
-// a scatter-add into U with FP64 atomics: its summation order varies from run
-// to run (results agree to rounding, not bit for bit).
+// a scatter-add into U in 128-bit fixed point (binary point at bit 64): every
+// contribution psi_i H_e (and y_i - 2 E psi_i) is split into an integer and a
+// 64-bit fraction and added with two integer atomics (the fraction's carry
+// counted exactly once), so the sum is exact up to the 2^-64 truncation of each
+// term and does not depend on the order of the additions -- the gradient is
+// bit-reproducible run to run.  The common factor g / sum psi^2 is applied once
+// per distinct configuration at the end.
 
 #include "cusci_internal.cuh"
 
@@ -93,27 +98,49 @@ __global__ void __launch_bounds__(RED)
     }
 }
 
+// adds c (|c| < 2^62) to the 128-bit fixed-point accumulator a[0] (fraction,
+// 2^-64 units) / a[1] (two's-complement integer part)
+__device__ __forceinline__ void fx_add(unsigned long long *a, double c) {
+    const double f = floor(c);
+    const long long ip = __double2ll_rz(f);                 // exact
+    const double frac = __dsub_rn(c, f);                      // exact, in [0, 1)
+    const unsigned long long lo = __double2ull_rz(__dmul_rn(frac, 18446744073709551616.0));
+    const unsigned long long old = atomicAdd(a, lo);
+    const unsigned long long carry = old + lo < old ? 1ull : 0ull;
+    atomicAdd(a + 1, (unsigned long long)ip + carry);
+}
+
 template <typename IDX>
 __global__ void __launch_bounds__(32 * LW)
-    le_scatter(const int64_t *__restrict__ off, int64_t n, const double *__restrict__ h,
-               const IDX *__restrict__ inv, const double *__restrict__ psi_u,
-               const double *__restrict__ y, const double *__restrict__ E,
-               const double *__restrict__ norm2, const double *__restrict__ gout,
-               double *__restrict__ grad_u) {
+    le_scatter_fx(const int64_t *__restrict__ off, int64_t n, const double *__restrict__ h,
+                  const IDX *__restrict__ inv, const double *__restrict__ psi_u,
+                  const double *__restrict__ y, const double *__restrict__ E,
+                  unsigned long long *__restrict__ acc) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * LW + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * LW;
-    const double scale = __ddiv_rn(gout ? *gout : 1.0, *norm2);
     const double e2 = __dmul_rn(2.0, *E);
     for (int64_t i = warp; i < n; i += nw) {
         const int64_t b = off[i], e = off[i + 1];
         if (b >= e) continue;
         const int64_t s = (int64_t)inv[b];
         const double p = __ldg(psi_u + s);
-        const double ps = __dmul_rn(p, scale);
         for (int64_t k = b + lane; k < e; k += 32)
-            atomicAdd(grad_u + (int64_t)inv[k], __dmul_rn(ps, h[k]));
-        if (lane == 0) atomicAdd(grad_u + s, __dmul_rn(scale, __dsub_rn(y[i], __dmul_rn(e2, p))));
+            fx_add(acc + 2 * (int64_t)inv[k], __dmul_rn(p, h[k]));
+        if (lane == 0) fx_add(acc + 2 * s, __dsub_rn(y[i], __dmul_rn(e2, p)));
+    }
+}
+
+// grad_u[u] = (g / sum psi^2) * (integer part + fraction) of the accumulator
+__global__ void le_finish_fx(const unsigned long long *__restrict__ acc, int64_t nu,
+                             const double *__restrict__ norm2, const double *__restrict__ gout,
+                             double *__restrict__ grad_u) {
+    const double scale = __ddiv_rn(gout ? *gout : 1.0, *norm2);
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const double v = __dadd_rn(__ll2double_rn((long long)acc[2 * u + 1]),
+                                   __dmul_rn(__ull2double_rn(acc[2 * u]), 5.421010862427522e-20));
+        grad_u[u] = __dmul_rn(scale, v);
     }
 }
 
@@ -168,6 +195,16 @@ extern "C" cusci_status cusci_local_energy_fwd(const int64_t *d_offsets, int64_t
     return CUSCI_OK;
 }
 
+extern "C" cusci_status cusci_local_energy_bwd_workspace(int64_t n, int64_t n_unique,
+                                                         size_t *bytes) {
+    if (!bytes || n < 0 || n_unique < 0)
+        return fail(CUSCI_ERR_INVALID, "cusci_local_energy_bwd_workspace: bad argument");
+    size_t rows = 0;
+    cusci_local_energy_workspace(n, &rows);
+    *bytes = rows + al((size_t)(n_unique > 0 ? n_unique : 1) * 16);
+    return CUSCI_OK;
+}
+
 extern "C" cusci_status cusci_local_energy_bwd(const int64_t *d_offsets, int64_t n,
                                                const double *d_h, const void *d_inverse,
                                                int index_bytes, const double *d_psi_u,
@@ -182,13 +219,14 @@ extern "C" cusci_status cusci_local_energy_bwd(const int64_t *d_offsets, int64_t
         return fail(CUSCI_ERR_INVALID, "cusci_local_energy_bwd: bad output");
     cudaStream_t st = (cudaStream_t)stream;
     const int grid = sm_count() * 8;
+    size_t need = 0, rows = 0;
+    cusci_local_energy_bwd_workspace(n, n_unique, &need);
+    cusci_local_energy_workspace(n, &rows);
+    if (!d_ws || ws_bytes < need)
+        return fail(CUSCI_ERR_OOM, "cusci_local_energy_bwd: workspace %zu < %zu", ws_bytes, need);
+    if ((uintptr_t)d_ws & 255u) return fail(CUSCI_ERR_INVALID, "local energy: workspace alignment");
     const double *y = d_y;
     if (!y) {
-        size_t need = 0;
-        cusci_local_energy_workspace(n, &need);
-        if (!d_ws || ws_bytes < need)
-            return fail(CUSCI_ERR_OOM, "cusci_local_energy_bwd: workspace %zu < %zu", ws_bytes,
-                        need);
         double *pq = (double *)d_ws;
         double *yw = (double *)((unsigned char *)d_ws + al((size_t)n * 16));
         if (index_bytes == 4)
@@ -200,16 +238,19 @@ extern "C" cusci_status cusci_local_energy_bwd(const int64_t *d_offsets, int64_t
         CUSCI_LAUNCHED(1, "local energy: rows");
         y = yw;
     }
-    cudaError_t e = cudaMemsetAsync(d_grad_u, 0, (size_t)n_unique * 8, st);
-    if (e != cudaSuccess) return cuda_fail(e, "local energy: clear gradient");
+    unsigned long long *acc = (unsigned long long *)((unsigned char *)d_ws + rows);
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)n_unique * 16, st);
+    if (e != cudaSuccess) return cuda_fail(e, "local energy: clear accumulators");
     if (index_bytes == 4)
-        le_scatter<int32_t><<<grid, 32 * LW, 0, st>>>(d_offsets, n, d_h,
-                                                      (const int32_t *)d_inverse, d_psi_u, y, d_E,
-                                                      d_norm2, d_grad_out, d_grad_u);
+        le_scatter_fx<int32_t><<<grid, 32 * LW, 0, st>>>(d_offsets, n, d_h,
+                                                         (const int32_t *)d_inverse, d_psi_u, y,
+                                                         d_E, acc);
     else
-        le_scatter<int64_t><<<grid, 32 * LW, 0, st>>>(d_offsets, n, d_h,
-                                                      (const int64_t *)d_inverse, d_psi_u, y, d_E,
-                                                      d_norm2, d_grad_out, d_grad_u);
-    CUSCI_LAUNCHED(1, "local energy backward");
+        le_scatter_fx<int64_t><<<grid, 32 * LW, 0, st>>>(d_offsets, n, d_h,
+                                                         (const int64_t *)d_inverse, d_psi_u, y,
+                                                         d_E, acc);
+    le_finish_fx<<<sm_count() * 4, 256, 0, st>>>(acc, n_unique, d_norm2, d_grad_out, d_grad_u);
+    CUSCI_LAUNCHED(2, "local energy backward");
+    CUSCI_LAUNCHED(2, "local energy backward");
     return CUSCI_OK;
 }

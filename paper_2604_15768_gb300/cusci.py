@@ -64,9 +64,13 @@ _PROTOS = {
     "cusci_batch_set_chunk": (_I, [_P, _I]),
     "cusci_batch_sources": (_I64, [_P]),
     "cusci_batch_count": (_I, [_P, _P, _D, _P, _P]),
+    "cusci_batch_set_grid": (_I, [_P, _I]),
+    "cusci_batch_dedup_workspace": (_I, [_P, _I64, ctypes.POINTER(_SZ)]),
+    "cusci_batch_dedup": (_I, [_P, _P, _P, _I64, _P, _SZ, _P, _P, _P, _P, _P]),
     "cusci_batch_gen": (_I, [_P, _P, _D, _P, _P, _P, _P, _P]),
     "cusci_local_energy_workspace": (_I, [_I64, ctypes.POINTER(_SZ)]),
     "cusci_local_energy_fwd": (_I, [_P, _I64, _P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "cusci_local_energy_bwd_workspace": (_I, [_I64, _I64, ctypes.POINTER(_SZ)]),
     "cusci_local_energy_bwd": (_I, [_P, _I64, _P, _P, _I, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ,
                                     _P]),
     "cusci_partition_plan": (_I, [_P, _I, _P, _I, _I, _P, _P, _P]),
@@ -423,12 +427,20 @@ def local_energy_fwd(offsets, h, inverse, psi_u, workspace=None, save_y=True, st
     return E, n2, y
 
 
+def local_energy_bwd_workspace(n: int, n_unique: int) -> int:
+    ws = ctypes.c_size_t()
+    _check(load().cusci_local_energy_bwd_workspace(int(n), int(n_unique), ctypes.byref(ws)),
+           "cusci_local_energy_bwd_workspace")
+    return ws.value
+
+
 def local_energy_bwd(offsets, h, inverse, psi_u, E, norm2, y=None, grad_out=None,
                      workspace=None, stream=None):
     n = offsets.shape[0] - 1
     ib = 4 if inverse.dtype == torch.int32 else 8
-    if y is None and (workspace is None or workspace.numel() < local_energy_workspace(n)):
-        workspace = torch.empty(local_energy_workspace(n), dtype=torch.uint8, device=h.device)
+    need = local_energy_bwd_workspace(n, psi_u.numel())
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=h.device)
     grad = torch.empty_like(psi_u)
     g = None if grad_out is None else grad_out.reshape(1).to(torch.float64).contiguous()
     _check(load().cusci_local_energy_bwd(_ptr(offsets), n, _ptr(h), _ptr(inverse), ib,
@@ -613,12 +625,14 @@ class Energy(torch.autograd.Function):
 
 
 class Batch:
-    """Many systems generated in one persistent launch (plus per-system dedup).
+    """Many systems generated in one persistent launch and de-duplicated in one
+    batched pass (every system's distinct set at once).
 
     ``plan()`` runs one untimed count/scan to size every buffer; ``run()``
-    issues count -> scan -> fill -> per-system dedup on the current stream with
-    no host synchronisation, so it can be captured with ``capture()`` in a CUDA
-    graph and replayed with ``replay()``.
+    issues count -> scan -> fill -> batched dedup on the current stream with no
+    host synchronisation, so it can be captured with ``capture()`` in a CUDA
+    graph and replayed with ``replay()``; the number of launches does not
+    depend on the number of systems.
     """
 
     def __init__(self, systems, dets_list, eps, chunk=8):
@@ -646,6 +660,10 @@ class Batch:
         _check(load().cusci_batch_set_chunk(self._h, int(chunk)), "cusci_batch_set_chunk")
         self.chunk = int(chunk)
 
+    def set_grid(self, blocks_per_sm):
+        _check(load().cusci_batch_set_grid(self._h, int(blocks_per_sm)), "cusci_batch_set_grid")
+        self.blocks_per_sm = int(blocks_per_sm)
+
     def count(self, counts, stream=None):
         _check(load().cusci_batch_count(self._h, _ptr(self.d_src), self.eps, _ptr(counts),
                                         _stream(stream)), "cusci_batch_count")
@@ -667,11 +685,10 @@ class Batch:
         self.out_d = torch.empty((max(self.total, 1), 2), dtype=torch.int64, device=dev)
         self.out_h = torch.empty(max(self.total, 1), dtype=torch.float64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
-        ws = 1
-        for k, s in enumerate(self.systems):
-            m = int(self.entry_begin[k + 1] - self.entry_begin[k])
-            ws = max(ws, dedup_workspace(max(m, 1), 2, s.M, s.n_alpha + s.n_beta))
-        self.dd_ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+        ws = ctypes.c_size_t()
+        _check(load().cusci_batch_dedup_workspace(self._h, self.total, ctypes.byref(ws)),
+               "cusci_batch_dedup_workspace")
+        self.dd_ws = torch.empty(max(ws.value, 1), dtype=torch.uint8, device=dev)
         self.unique = torch.empty((max(self.total, 1), 2), dtype=torch.int64, device=dev)
         self.inverse = torch.empty(max(self.total, 1), dtype=torch.int32, device=dev)
         self.n_unique = torch.zeros(len(self.systems), dtype=torch.int64, device=dev)
@@ -681,33 +698,36 @@ class Batch:
         self.count(self.counts, stream)
         exclusive_scan(self.counts, out=self.offsets, workspace=self.scan_ws, stream=stream)
         self.gen(self.offsets, self.out_d, self.out_h, self.status, stream)
-        for k, s in enumerate(self.systems):
-            a, b = int(self.entry_begin[k]), int(self.entry_begin[k + 1])
-            if b == a:
-                continue
-            # two-word keys; for one-word systems (M <= 64) the library sorts word 0 only
-            dedup_into(self.out_d[a:b], s.M, s.n_alpha + s.n_beta, self.unique[a:b],
-                       self.inverse[a:b], self.n_unique[k:k + 1], self.dd_ws, stream=stream)
+        _check(load().cusci_batch_dedup(self._h, _ptr(self.offsets), _ptr(self.out_d), self.total,
+                                        _ptr(self.dd_ws), self.dd_ws.numel(), _ptr(self.unique),
+                                        _ptr(self.inverse), _ptr(self.n_unique),
+                                        _ptr(self.status), _stream(stream)), "cusci_batch_dedup")
 
-    def autotune(self, candidates=(1, 2, 4, 8, 16, 32, 64), reps=2):
-        """Pick the work-item size (sources per item) with the fastest fill launch."""
+    def autotune(self, candidates=(1, 2, 4, 8, 16, 32, 64), grids=(4, 8, 16), reps=2):
+        """Pick the work-item size (sources per item) and the persistent grid
+        (blocks per SM) with the fastest whole run (count, scan, fill and
+        batched dedup).  Returns ((chunk, blocks_per_sm), ms)."""
         best = None
-        for c in candidates:
-            self.set_chunk(c)
-            self.gen(self.offsets, self.out_d, self.out_h, self.status)
-            torch.cuda.synchronize()
-            t = []
-            for _ in range(reps):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                self.gen(self.offsets, self.out_d, self.out_h, self.status)
-                b.record()
+        for g in grids:
+            self.set_grid(g)
+            for c in candidates:
+                self.set_chunk(c)
+                self.run()
                 torch.cuda.synchronize()
-                t.append(a.elapsed_time(b))
-            ms = min(t)
-            if best is None or ms < best[1]:
-                best = (c, ms)
-        self.set_chunk(best[0])
+                t = []
+                for _ in range(reps):
+                    a, b = (torch.cuda.Event(enable_timing=True),
+                            torch.cuda.Event(enable_timing=True))
+                    a.record()
+                    self.run()
+                    b.record()
+                    torch.cuda.synchronize()
+                    t.append(a.elapsed_time(b))
+                ms = min(t)
+                if best is None or ms < best[1]:
+                    best = ((c, g), ms)
+        self.set_chunk(best[0][0])
+        self.set_grid(best[0][1])
         return best
 
     def capture(self):

@@ -71,8 +71,8 @@ def test_batch_matches_single_system_path(batch):
 
 def test_batch_graph_replay_and_autotune(batch):
     systems, b = batch
-    best_chunk, ms = b.autotune(candidates=(1, 4, 16), reps=1)
-    assert best_chunk in (1, 4, 16) and ms > 0
+    (best_chunk, best_grid), ms = b.autotune(candidates=(1, 4, 16), grids=(4, 8), reps=1)
+    assert best_chunk in (1, 4, 16) and best_grid in (4, 8) and ms > 0
     b.capture()
     b.out_h.zero_()
     b.inverse.zero_()

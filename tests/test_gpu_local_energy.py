@@ -36,6 +36,10 @@ def test_local_energy_matches_oracle(index_bytes):
     assert np.abs(y.cpu().numpy() - oy).max() <= 1e-10
     assert np.abs(grad.cpu().numpy() - og).max() <= 1e-10
     assert np.abs(grad2.cpu().numpy() - og).max() <= 1e-10
+    # the fixed-point scatter makes the adjoint bit-reproducible
+    grad3 = cusci.local_energy_bwd(off, oh, inv, dpsi, E, n2, y=y)
+    assert np.array_equal(grad.cpu().numpy(), grad2.cpu().numpy())
+    assert np.array_equal(grad.cpu().numpy(), grad3.cpu().numpy())
 
 
 def test_local_energy_autograd_finite_differences():
