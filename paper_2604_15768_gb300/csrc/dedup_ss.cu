@@ -19,13 +19,13 @@
 //     pages and L2 lines.  Slots inside a run are handed out with
 //     warp-aggregated shared-memory atomics; the slot of every entry is kept
 //     (4 B) so the reverse index can be gathered back later.
-//  3. Each leaf is loaded into shared memory, packed as
-//     (key - leaf_min) << pos_bits | position, LSD radix-sorted there (stable
-//     8-bit passes over the key bits only; a pass whose digit is constant is
-//     skipped; the next digit's histogram is built while scattering), and
-//     walked once to mark run heads: the local unique id of every position and
-//     the distinct keys.  Leaves that do not fit are sorted in global memory
-//     with their positions in a separate array.
+//  3. Each leaf is de-duplicated in shared memory: every entry is inserted
+//     into an open-addressing hash table (its slot kept), the few distinct
+//     keys are compacted, packed as (key - leaf_min) << 12 | slot and ordered
+//     (rank counting for up to 512 of them, 8-bit LSD passes otherwise), and
+//     every entry reads its local unique id back through its slot.  Leaves
+//     that are too large or too diverse are LSD-sorted in global memory with
+//     their positions in a separate array and walked for run heads.
 //  4. A scan of per-leaf distinct counts gives the global unique ids; the
 //     distinct keys are compacted, and the reverse index is gathered back
 //     through the two stored slot arrays -- reads with the same locality as
@@ -51,7 +51,6 @@ constexpr int WARPS = T / 32;
 constexpr int B2 = 256;
 constexpr int LOG2_B2 = 8;
 constexpr int OVS = 4;
-constexpr int LEAF_CAP = 4096;
 constexpr int LEAF_AVG = 1600;
 constexpr int MAX_B1 = 4096;
 constexpr int BT_MAX = 2048;      // binomial-table entries staged in shared memory
@@ -629,23 +628,42 @@ __global__ void __launch_bounds__(T)
     }
 }
 
-struct LeafSmem {
-    uint64_t A[LEAF_CAP];
-    uint64_t B[LEAF_CAP];
+// Leaf de-duplication.  A leaf of at most HT entries is de-duplicated through
+// an open-addressing hash table in shared memory (one probe sequence per entry,
+// no sort of the entries themselves): the distinct keys are then compacted,
+// packed as (key - leaf_min) << LG_HT | slot and ordered -- by counting ranks
+// when there are few of them, by LSD radix passes otherwise -- and every entry
+// reads its rank back through its slot.  Leaves with more entries, more than
+// HASH_D distinct keys, a key equal to the empty marker or a key range too
+// wide to pack are LSD-sorted in global memory with their positions alongside.
+constexpr int LG_HT = 12;
+constexpr int HT = 1 << LG_HT;     // table slots, and entries of a leaf on the hash path
+constexpr int HASH_D = HT / 2;     // distinct keys a leaf may hold on the hash path (load <= 1/2)
+constexpr int COUNT_D = 512;       // distinct keys ranked by counting; more are radix-sorted
+constexpr uint64_t EMPTY = ~0ull;  // marker of a free table slot
+
+struct LsdScratch {
     uint32_t hist[256];
     uint32_t hnext[256];  // histogram of the next pass's digit, built while scattering
     uint32_t run[256];
     uint32_t ttot[256];
     uint16_t wcnt[WARPS][256];
-    uint64_t red_lo[WARPS], red_hi[WARPS];
-    uint32_t red_cnt[WARPS];
+    uint32_t flag;
 };
 
-// one pass of a stable LSD radix sort of a[0..n) into b[0..n) on the 8-bit
-// digit at `shift`; pa / pb: optional 32-bit payload moved along (a, b, pa, pb
-// in shared or global memory)
-template <bool PAYLOAD>
-__device__ void leaf_hist(const uint64_t *a, int64_t n, int shift, uint32_t *hist) {
+struct LeafSmem {
+    uint64_t tab[HT];  // hash table; afterwards the two sort buffers tab and tab + HASH_D
+    uint16_t es[HT];   // table slot of every entry of the leaf
+    union {
+        LsdScratch L;
+        uint16_t sl[HT];  // rank of the key held in every slot (written after ordering)
+    } u;
+    uint64_t red_lo[WARPS], red_hi[WARPS];
+    uint32_t red_cnt[WARPS];
+    uint32_t nd, bad;
+};
+
+__device__ __forceinline__ void leaf_hist(const uint64_t *a, int64_t n, int shift, uint32_t *hist) {
     for (int d = threadIdx.x; d < 256; d += T) hist[d] = 0;
     __syncthreads();
     for (int64_t k = threadIdx.x; k < n; k += T) atomicAdd(&hist[(a[k] >> shift) & 255], 1u);
@@ -654,32 +672,32 @@ __device__ void leaf_hist(const uint64_t *a, int64_t n, int shift, uint32_t *his
 
 // One pass of a stable LSD radix sort of a[0..n) into b[0..n) on the 8-bit
 // digit at `shift`; pa / pb: optional 32-bit payload moved along (a, b, pa, pb
-// in shared or global memory).  S.hist must hold this digit's histogram; when
+// in shared or global memory).  L.hist must hold this digit's histogram; when
 // next_shift >= 0 the histogram of the digit at next_shift is built into
-// S.hnext while scattering.  Returns false (and moves nothing) when every key
+// L.hnext while scattering.  Returns false (and moves nothing) when every key
 // has the same digit.
 template <bool PAYLOAD>
 __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, uint32_t *pb,
-                          int64_t n, int shift, int next_shift, LeafSmem &S) {
+                          int64_t n, int shift, int next_shift, LsdScratch &L) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) S.red_cnt[0] = 0;
-    for (int d = threadIdx.x; d < 256; d += T) S.hnext[d] = 0;
+    if (threadIdx.x == 0) L.flag = 0;
+    for (int d = threadIdx.x; d < 256; d += T) L.hnext[d] = 0;
     __syncthreads();
     for (int d = threadIdx.x; d < 256; d += T)
-        if (S.hist[d] == (uint32_t)n) S.red_cnt[0] = 1;
+        if (L.hist[d] == (uint32_t)n) L.flag = 1;
     __syncthreads();
-    if (S.red_cnt[0]) {
+    if (L.flag) {
         // nothing moves; the next digit's histogram still has to be built
         if (next_shift >= 0)
             for (int64_t k = threadIdx.x; k < n; k += T)
-                atomicAdd(&S.hnext[(a[k] >> next_shift) & 255], 1u);
+                atomicAdd(&L.hnext[(a[k] >> next_shift) & 255], 1u);
         __syncthreads();
         return false;
     }
     if (wid == 0) {
         uint32_t c[8], s = 0;
 #pragma unroll
-        for (int q = 0; q < 8; q++) { c[q] = S.hist[lane * 8 + q]; s += c[q]; }
+        for (int q = 0; q < 8; q++) { c[q] = L.hist[lane * 8 + q]; s += c[q]; }
         uint32_t inc = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -688,11 +706,11 @@ __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, ui
         }
         uint32_t ex = inc - s;
 #pragma unroll
-        for (int q = 0; q < 8; q++) { S.run[lane * 8 + q] = ex; ex += c[q]; }
+        for (int q = 0; q < 8; q++) { L.run[lane * 8 + q] = ex; ex += c[q]; }
     }
     __syncthreads();
     for (int64_t t0 = 0; t0 < n; t0 += LTILE) {
-        for (int q = threadIdx.x; q < WARPS * 256; q += T) (&S.wcnt[0][0])[q] = 0;
+        for (int q = threadIdx.x; q < WARPS * 256; q += T) (&L.wcnt[0][0])[q] = 0;
         __syncthreads();
         uint64_t v[LRI];
         uint32_t dg[LRI], rk[LRI];
@@ -711,10 +729,10 @@ __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, ui
             if (wbase + r * 32 >= n) continue;  // whole round past the end (warp-uniform)
             const unsigned peers = __match_any_sync(FULL, dg[r]);
             const int below = __popc(peers & ((1u << lane) - 1u));
-            uint32_t prev = valid ? S.wcnt[wid][dg[r]] : 0;
+            uint32_t prev = valid ? L.wcnt[wid][dg[r]] : 0;
             rk[r] = prev + below;
             __syncwarp();
-            if (valid && below == 0) S.wcnt[wid][dg[r]] = (uint16_t)(prev + __popc(peers));
+            if (valid && below == 0) L.wcnt[wid][dg[r]] = (uint16_t)(prev + __popc(peers));
             __syncwarp();
         }
         __syncthreads();
@@ -722,24 +740,24 @@ __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, ui
             uint32_t s = 0;
 #pragma unroll
             for (int w = 0; w < WARPS; w++) {
-                const uint32_t c = S.wcnt[w][d];
-                S.wcnt[w][d] = (uint16_t)s;
+                const uint32_t c = L.wcnt[w][d];
+                L.wcnt[w][d] = (uint16_t)s;
                 s += c;
             }
-            S.ttot[d] = s;
+            L.ttot[d] = s;
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < LRI; r++) {
             if (dg[r] < 256) {
-                const uint32_t dst = S.run[dg[r]] + S.wcnt[wid][dg[r]] + rk[r];
+                const uint32_t dst = L.run[dg[r]] + L.wcnt[wid][dg[r]] + rk[r];
                 b[dst] = v[r];
                 if (PAYLOAD) pb[dst] = pa[t0 + wid * (LRI * 32) + r * 32 + lane];
-                if (next_shift >= 0) atomicAdd(&S.hnext[(v[r] >> next_shift) & 255], 1u);
+                if (next_shift >= 0) atomicAdd(&L.hnext[(v[r] >> next_shift) & 255], 1u);
             }
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < 256; d += T) S.run[d] += S.ttot[d];
+        for (int d = threadIdx.x; d < 256; d += T) L.run[d] += L.ttot[d];
         __syncthreads();
     }
     return true;
@@ -749,16 +767,16 @@ __device__ bool leaf_pass(const uint64_t *a, uint64_t *b, const uint32_t *pa, ui
 // returns the buffer holding the sorted keys
 template <bool PAYLOAD>
 __device__ uint64_t *leaf_sort_bits(uint64_t *a, uint64_t *b, uint32_t *&pa, uint32_t *&pb,
-                                    int64_t n, int lo, int hi, LeafSmem &S) {
+                                    int64_t n, int lo, int hi, LsdScratch &L) {
     if (lo >= hi) return a;
-    leaf_hist<PAYLOAD>(a, n, lo, S.hist);
+    leaf_hist(a, n, lo, L.hist);
     for (int shift = lo; shift < hi; shift += 8) {
         const int next = shift + 8 < hi ? shift + 8 : -1;
-        if (leaf_pass<PAYLOAD>(a, b, pa, pb, n, shift, next, S)) {
+        if (leaf_pass<PAYLOAD>(a, b, pa, pb, n, shift, next, L)) {
             uint64_t *t = a; a = b; b = t;
             if (PAYLOAD) { uint32_t *tp = pa; pa = pb; pb = tp; }
         }
-        for (int d = threadIdx.x; d < 256; d += T) S.hist[d] = S.hnext[d];
+        for (int d = threadIdx.x; d < 256; d += T) L.hist[d] = L.hnext[d];
         __syncthreads();
     }
     return a;
@@ -809,11 +827,88 @@ __device__ void leaf_walk(const uint64_t *a, const uint32_t *pos, int64_t n, int
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(T, 3)
-    leaf_sort(uint64_t *__restrict__ K2, uint64_t *__restrict__ scratch,
-              uint32_t *__restrict__ pay, int64_t N, int64_t NL,
-              const int64_t *__restrict__ leaf_start, uint32_t *__restrict__ U2,
-              uint64_t *__restrict__ tmpU, int64_t *__restrict__ ucnt) {
+// block-wide minimum and maximum of one value per thread (through S.red_lo/hi)
+__device__ __forceinline__ void block_min_max(uint64_t lo, uint64_t hi, LeafSmem &S,
+                                              uint64_t &r_lo, uint64_t &r_hi) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(FULL, lo, o), z = __shfl_xor_sync(FULL, hi, o);
+        lo = y < lo ? y : lo;
+        hi = z > hi ? z : hi;
+    }
+    if (lane == 0) { S.red_lo[wid] = lo; S.red_hi[wid] = hi; }
+    __syncthreads();
+    r_lo = S.red_lo[0];
+    r_hi = S.red_hi[0];
+    for (int w = 1; w < WARPS; w++) {
+        r_lo = S.red_lo[w] < r_lo ? S.red_lo[w] : r_lo;
+        r_hi = S.red_hi[w] > r_hi ? S.red_hi[w] : r_hi;
+    }
+}
+
+// a leaf off the hash path: keys (key - min) LSD-sorted in global memory with
+// their positions in a separate array, then walked for run heads
+__device__ void leaf_global(uint64_t *__restrict__ K2, uint64_t *__restrict__ scratch,
+                            uint32_t *__restrict__ pay, int64_t N, int64_t ls, int64_t n,
+                            uint32_t *__restrict__ U2, uint64_t *__restrict__ tmpU,
+                            int64_t *__restrict__ ucnt_out, LeafSmem &S) {
+    uint64_t lo = ~0ull, hi = 0;
+    for (int64_t k = threadIdx.x; k < n; k += T) {
+        const uint64_t x = K2[ls + k];
+        lo = x < lo ? x : lo;
+        hi = x > hi ? x : hi;
+    }
+    uint64_t r_lo, r_hi;
+    block_min_max(lo, hi, S, r_lo, r_hi);
+    const int rb = r_hi == r_lo ? 0 : 64 - __clzll((long long)(r_hi - r_lo));
+    uint64_t *a = K2 + ls, *b = scratch + ls;
+    uint32_t *pa = pay + ls, *pb = pay + N + ls;
+    for (int64_t k = threadIdx.x; k < n; k += T) {
+        a[k] = K2[ls + k] - r_lo;
+        pa[k] = (uint32_t)k;
+    }
+    __syncthreads();
+    a = leaf_sort_bits<true>(a, b, pa, pb, n, 0, rb, S.u.L);
+    leaf_walk(a, pa, n, 0, r_lo, ls, U2, tmpU, ucnt_out, S);
+}
+
+// slot of key x in the table of 2^lg slots, inserting it if absent (linear
+// probing; at most 2^lg probes).  Sets S.bad when x is the empty marker, when
+// the leaf exceeds HASH_D distinct keys, or when no slot was found.
+__device__ __forceinline__ uint32_t hash_insert_slot(uint64_t x, int lg, LeafSmem &S) {
+    if (x == EMPTY) {
+        S.bad = 1;
+        return 0;
+    }
+    volatile uint64_t *vt = S.tab;
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = (uint32_t)((x * 0x9E3779B97F4A7C15ull) >> (64 - lg));
+    for (uint32_t i = 0; i <= mask; i++) {
+        uint64_t cur = vt[s];
+        if (cur == EMPTY) {
+            cur = atomicCAS((unsigned long long *)&S.tab[s], (unsigned long long)EMPTY,
+                            (unsigned long long)x);
+            if (cur == EMPTY) {
+                if (atomicAdd(&S.nd, 1u) >= (uint32_t)HASH_D) S.bad = 1;
+                return s;
+            }
+        }
+        if (cur == x) return s;
+        s = (s + 1) & mask;
+    }
+    S.bad = 1;
+    return 0;
+}
+
+constexpr int HPT = HT / T;  // table slots per thread in the compaction
+constexpr int UI = 4;        // keys in flight per thread in the insertion
+
+__global__ void __launch_bounds__(T, 4)
+    leaf_dedup(uint64_t *__restrict__ K2, uint64_t *__restrict__ scratch,
+               uint32_t *__restrict__ pay, int64_t N, int64_t NL,
+               const int64_t *__restrict__ leaf_start, uint32_t *__restrict__ U2,
+               uint64_t *__restrict__ tmpU, int64_t *__restrict__ ucnt) {
     extern __shared__ __align__(16) unsigned char sm[];
     LeafSmem &S = *reinterpret_cast<LeafSmem *>(sm);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -824,48 +919,115 @@ __global__ void __launch_bounds__(T, 3)
             if (threadIdx.x == 0) ucnt[leaf] = 0;
             continue;
         }
-        uint64_t lo = ~0ull, hi = 0;
-        for (int64_t k = threadIdx.x; k < n; k += T) {
-            const uint64_t x = K2[ls + k];
-            lo = x < lo ? x : lo;
-            hi = x > hi ? x : hi;
+        if (n > HT) {
+            leaf_global(K2, scratch, pay, N, ls, n, U2, tmpU, ucnt + leaf, S);
+            continue;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t y = __shfl_xor_sync(FULL, lo, o), z = __shfl_xor_sync(FULL, hi, o);
-            lo = y < lo ? y : lo;
-            hi = z > hi ? z : hi;
+        // table of 2^lg >= 2n slots (64 at least, HT at most)
+        int lg = (n <= 1 ? 0 : 64 - __clzll((long long)(n - 1))) + 1;
+        lg = lg < 6 ? 6 : (lg > LG_HT ? LG_HT : lg);
+        const int TS = 1 << lg;
+        for (int s = threadIdx.x; s < TS; s += T) S.tab[s] = EMPTY;
+        if (threadIdx.x == 0) {
+            S.nd = 0;
+            S.bad = 0;
         }
-        if (lane == 0) { S.red_lo[wid] = lo; S.red_hi[wid] = hi; }
         __syncthreads();
-        uint64_t r_lo = S.red_lo[0], r_hi = S.red_hi[0];
-        for (int w = 1; w < WARPS; w++) {
-            r_lo = S.red_lo[w] < r_lo ? S.red_lo[w] : r_lo;
-            r_hi = S.red_hi[w] > r_hi ? S.red_hi[w] : r_hi;
-        }
-        const int rb = r_hi == r_lo ? 0 : 64 - __clzll((long long)(r_hi - r_lo));
-        const int pbits = n <= 1 ? 0 : 64 - __clzll((long long)(n - 1));
-        if (n <= LEAF_CAP && rb + pbits <= 64) {
-            // packed (key - min) << pbits | position, sorted in shared memory
-            uint64_t *a = S.A, *b = S.B;
-            for (int64_t k = threadIdx.x; k < n; k += T)
-                a[k] = ((K2[ls + k] - r_lo) << pbits) | (uint64_t)k;
-            __syncthreads();
-            uint32_t *np = nullptr, *nq = nullptr;
-            a = leaf_sort_bits<false>(a, b, np, nq, n, pbits, pbits + rb, S);
-            leaf_walk(a, nullptr, n, pbits, r_lo, ls, U2, tmpU, ucnt + leaf, S);
-        } else {
-            // global memory: keys (key - min) with positions in a separate array
-            uint64_t *a = K2 + ls, *b = scratch + ls;
-            uint32_t *pa = pay + ls, *pb = pay + N + ls;
-            for (int64_t k = threadIdx.x; k < n; k += T) {
-                a[k] = K2[ls + k] - r_lo;
-                pa[k] = (uint32_t)k;
+        // 1. insert every entry, remembering its slot
+        for (int64_t k0 = 0; k0 < n; k0 += T * UI) {
+            uint64_t x[UI];
+#pragma unroll
+            for (int u = 0; u < UI; u++) {
+                const int64_t k = k0 + u * T + threadIdx.x;
+                x[u] = k < n ? K2[ls + k] : 0;
             }
-            __syncthreads();
-            a = leaf_sort_bits<true>(a, b, pa, pb, n, 0, rb, S);
-            leaf_walk(a, pa, n, 0, r_lo, ls, U2, tmpU, ucnt + leaf, S);
+#pragma unroll
+            for (int u = 0; u < UI; u++) {
+                const int64_t k = k0 + u * T + threadIdx.x;
+                if (k < n) S.es[k] = (uint16_t)hash_insert_slot(x[u], lg, S);
+            }
         }
+        __syncthreads();
+        if (S.bad) {
+            leaf_global(K2, scratch, pay, N, ls, n, U2, tmpU, ucnt + leaf, S);
+            continue;
+        }
+        const int d = (int)S.nd;
+        // 2. compact the distinct keys (read all slots first: the packed keys
+        //    overwrite the front of the table)
+        uint64_t v[HPT];
+        uint64_t lo = ~0ull, hi = 0;
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int j = 0; j < HPT; j++) {
+            const int s = j * T + threadIdx.x;
+            v[j] = s < TS ? S.tab[s] : EMPTY;
+            if (v[j] != EMPTY) {
+                lo = v[j] < lo ? v[j] : lo;
+                hi = v[j] > hi ? v[j] : hi;
+                cnt++;
+            }
+        }
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) S.red_cnt[wid] = inc;
+        uint64_t r_lo, r_hi;
+        block_min_max(lo, hi, S, r_lo, r_hi);  // its barrier also publishes red_cnt
+        const int rb = r_hi == r_lo ? 0 : 64 - __clzll((long long)(r_hi - r_lo));
+        if (rb + LG_HT > 64) {
+            __syncthreads();  // every thread has read the reductions
+            leaf_global(K2, scratch, pay, N, ls, n, U2, tmpU, ucnt + leaf, S);
+            continue;
+        }
+        uint32_t pos = inc - cnt;
+        for (int w = 0; w < wid; w++) pos += S.red_cnt[w];
+#pragma unroll
+        for (int j = 0; j < HPT; j++) {
+            if (v[j] != EMPTY) {
+                const uint64_t s = (uint64_t)(j * T + threadIdx.x);
+                S.tab[pos++] = ((v[j] - r_lo) << LG_HT) | s;
+            }
+        }
+        __syncthreads();
+        // 3. order the d distinct keys; write each slot's rank and the keys
+        if (d <= COUNT_D) {
+            const uint64_t *a = S.tab;
+            const int i0 = threadIdx.x, i1 = threadIdx.x + T;
+            const uint64_t m0 = i0 < d ? a[i0] : 0, m1 = i1 < d ? a[i1] : 0;
+            uint32_t r0 = 0, r1 = 0;
+            for (int j = 0; j < d; j++) {
+                const uint64_t y = a[j];
+                r0 += y < m0;
+                r1 += y < m1;
+            }
+            if (i0 < d) {
+                S.u.sl[m0 & (HT - 1)] = (uint16_t)r0;
+                tmpU[ls + r0] = (m0 >> LG_HT) + r_lo;
+            }
+            if (i1 < d) {
+                S.u.sl[m1 & (HT - 1)] = (uint16_t)r1;
+                tmpU[ls + r1] = (m1 >> LG_HT) + r_lo;
+            }
+        } else {
+            uint32_t *np = nullptr, *nq = nullptr;
+            const uint64_t *a =
+                leaf_sort_bits<false>(S.tab, S.tab + HASH_D, np, nq, d, LG_HT, LG_HT + rb, S.u.L);
+            // the radix passes end with a barrier: their scratch may now hold sl
+            for (int r = threadIdx.x; r < d; r += T) {
+                const uint64_t m = a[r];
+                S.u.sl[m & (HT - 1)] = (uint16_t)r;
+                tmpU[ls + r] = (m >> LG_HT) + r_lo;
+            }
+        }
+        __syncthreads();
+        // 4. the local unique id of every entry
+        for (int k = threadIdx.x; k < (int)n; k += T) U2[ls + k] = S.u.sl[S.es[k]];
+        if (threadIdx.x == 0) ucnt[leaf] = d;
+        __syncthreads();  // before the next leaf resets the table
     }
 }
 
@@ -1022,7 +1184,7 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
                                       what);
         if (rc0 == CUSCI_OK)
             rc0 = allow_smem((const void *)scatter1<W>, (size_t)MAX_B1 * 4 + BT_MAX * 8, what);
-        if (rc0 == CUSCI_OK) rc0 = allow_smem((const void *)leaf_sort, sizeof(LeafSmem), what);
+        if (rc0 == CUSCI_OK) rc0 = allow_smem((const void *)leaf_dedup, sizeof(LeafSmem), what);
         if (rc0 != CUSCI_OK) return rc0;
     }
     hist1<W><<<p.G, T, sm_h1, st>>>(keys, p.N, p.per_cta, p.mode, p.n_bits, p.n_ones, p.kcols, bt,
@@ -1041,7 +1203,7 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
     launches++;
     // leaves
     uint32_t *pay = (uint32_t *)(ws + p.o_pay);
-    leaf_sort<<<sms * 3, T, sizeof(LeafSmem), st>>>(K2, K1, pay, p.N, p.NL, leafst, U2, tmpU, ucnt);
+    leaf_dedup<<<sms * 4, T, sizeof(LeafSmem), st>>>(K2, K1, pay, p.N, p.NL, leafst, U2, tmpU, ucnt);
     launches++;
     rc = exclusive_scan_i64(ucnt, p.NL, ubase, scanws, st);
     if (rc != CUSCI_OK) return rc;

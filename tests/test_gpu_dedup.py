@@ -182,18 +182,33 @@ def test_sample_sort_wide_and_overflowing_leaves_vs_oracle():
     wide |= rng.integers(0, 2, size=n).astype(np.uint64)
     wide[::4] = wide[1::4][: wide[::4].size]
     compare(wide.reshape(-1, 1), 64, -1)
-    # sample positions floor(j * N / NS), NS = 4 samples per leaf, leaves =
-    # 128 per level-1 bucket, level-1 buckets = the power of two covering
-    # N / 2048 / 128 (the plan of the sample-sort path).  Two heavy keys take
-    # turns at those positions, so one leaf spans (2^39, 2^41] with every
+    # sample positions floor(j * N / NS): NS = 4 samples per leaf, 256 leaves
+    # per level-1 bucket, level-1 buckets = the power of two covering
+    # ceil(N / 1600) / 256 (the plan of the sample-sort path).  Two heavy keys
+    # take turns at those positions, so one leaf spans (2^39, 2^41) with every
     # distinct key inside: narrow enough for the hash path, too many keys.
-    leaves_wanted = -(-n // 2048)
+    leaves_wanted = -(-n // 1600)
     b1 = 1
-    while b1 < -(-leaves_wanted // 128):
+    while b1 < -(-leaves_wanted // 256):
         b1 *= 2
-    ns = min(b1 * 128 * 4, n)
+    ns = min(b1 * 256 * 4, n)
     keys = np.uint64(1 << 40) + rng.permutation(n).astype(np.uint64) * np.uint64(3)
     at = (np.arange(ns, dtype=np.int64) * n) // ns
     keys[at[0::2]] = np.uint64(1 << 39)
     keys[at[1::2]] = np.uint64(1 << 41)
     compare(keys.reshape(-1, 1), 42, -1)
+
+
+def test_sample_sort_hash_path_limits_vs_oracle():
+    """Leaves at the limits of the shared-memory hash path: (1) all-distinct
+    keys, so that leaves hold 512..2048 distinct keys (radix-ordered) or more
+    than 2048 (too many for the table: sorted in global memory); (2) keys in a
+    narrow range at the top of the 64-bit space including the all-ones word,
+    which is the table's empty marker and sends its leaf to global memory."""
+    rng = np.random.default_rng(21)
+    n = 4_600_000
+    keys = rng.choice(1 << 40, size=n, replace=False).astype(np.uint64)
+    compare(keys.reshape(-1, 1), 40, -1)
+    top = np.uint64(0xFFFFFFFFFFFFFFFF) - rng.integers(0, 1 << 30, size=n).astype(np.uint64)
+    top[rng.choice(n, 20_000, replace=False)] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    compare(top.reshape(-1, 1), 64, -1)
