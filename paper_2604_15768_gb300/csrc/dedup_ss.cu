@@ -17,12 +17,12 @@
 //     writes its chunk's entries into per-bucket runs inside its own contiguous
 //     region, so its write fronts and the later gathers stay inside a few TLB
 //     pages and L2 lines.  Slots inside a run are handed out with
-//     warp-aggregated shared-memory atomics; the slot of every entry is kept
+//     shared-memory atomics; the slot of every entry is kept
 //     (4 B) so the reverse index can be gathered back later.
 //  3. Each leaf is de-duplicated in shared memory: every entry is inserted
 //     into an open-addressing hash table (its slot kept), the few distinct
 //     keys are compacted, packed as (key - leaf_min) << 12 | slot and ordered
-//     (rank counting for up to 512 of them, 8-bit LSD passes otherwise), and
+//     (rank counting for up to 256 of them, 8-bit LSD passes otherwise), and
 //     every entry reads its local unique id back through its slot.  Leaves
 //     that are too large or too diverse are LSD-sorted in global memory with
 //     their positions in a separate array and walked for run heads.
@@ -420,19 +420,6 @@ __global__ void widen_u32(const uint32_t *__restrict__ h, int64_t n, int64_t *__
         o[k] = h[k];
 }
 
-// warp-aggregated slot reservation: lanes with the same bucket b get
-// consecutive slots from the shared counter run[b]
-__device__ __forceinline__ uint64_t reserve_slot(unsigned long long *run, uint32_t b, bool valid,
-                                                 int lane) {
-    const unsigned peers = __match_any_sync(FULL, b);
-    const int leader = __ffs(peers) - 1;
-    const int below = __popc(peers & ((1u << lane) - 1u));
-    unsigned long long base = 0;
-    if (valid && lane == leader) base = atomicAdd(&run[b], (unsigned long long)__popc(peers));
-    base = __shfl_sync(FULL, base, leader);
-    return base + below;
-}
-
 // exclusive scan of a shared-memory array v[0..n), in place; every thread of
 // the block takes part
 __device__ void block_excl_scan_smem(uint32_t *v, int n, uint32_t *warp_tot) {
@@ -535,7 +522,7 @@ __global__ void __launch_bounds__(T)
            int64_t *__restrict__ leaf_start) {
     __shared__ uint64_t L[B2];
     __shared__ uint32_t h[B2];
-    __shared__ unsigned long long run[B2];
+    __shared__ uint32_t run[B2];  // next free slot of every leaf, relative to kbase[b1]
     __shared__ uint16_t T2[(1 << LG_CELLS2) + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int b1 = blockIdx.x;
@@ -591,7 +578,7 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
         for (int q = 0; q < PER; q++) {
             const int t = lane * PER + q;
-            run[t] = (unsigned long long)(kb + ex);
+            run[t] = ex;
             leaf_start[(int64_t)b1 * B2 + t] = kb + ex;
             ex += cnt[q];
         }
@@ -617,9 +604,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
             for (int u = 0; u < U1; u++) {
                 const int64_t k = k0 + u * 32 + lane;
-                const bool valid = k < len;
-                const uint64_t d = reserve_slot(run, bb[u], valid, lane);
-                if (valid) {
+                if (k < len) {
+                    const uint64_t d = (uint64_t)kb + atomicAdd(&run[bb[u]], 1u);
                     K2[d] = x[u];
                     dest2[sb + k] = (uint32_t)d;
                 }
@@ -639,7 +625,7 @@ __global__ void __launch_bounds__(T)
 constexpr int LG_HT = 12;
 constexpr int HT = 1 << LG_HT;     // table slots, and entries of a leaf on the hash path
 constexpr int HASH_D = HT / 2;     // distinct keys a leaf may hold on the hash path (load <= 1/2)
-constexpr int COUNT_D = 512;       // distinct keys ranked by counting; more are radix-sorted
+constexpr int COUNT_D = T;         // distinct keys ranked by counting; more are radix-sorted
 constexpr uint64_t EMPTY = ~0ull;  // marker of a free table slot
 
 struct LsdScratch {
@@ -992,25 +978,39 @@ __global__ void __launch_bounds__(T, 4)
                 S.tab[pos++] = ((v[j] - r_lo) << LG_HT) | s;
             }
         }
+        // rank counters of the counting path, behind the packed keys (d <= T)
+        uint32_t *rank = reinterpret_cast<uint32_t *>(S.tab + HASH_D);
+        if (d <= COUNT_D && threadIdx.x < d) rank[threadIdx.x] = 0;
         __syncthreads();
         // 3. order the d distinct keys; write each slot's rank and the keys
         if (d <= COUNT_D) {
+            // key chunk c (32 keys, one per lane) against a share of all d keys:
+            // the C = ceil(d/32) chunks split the block's warps between them
             const uint64_t *a = S.tab;
-            const int i0 = threadIdx.x, i1 = threadIdx.x + T;
-            const uint64_t m0 = i0 < d ? a[i0] : 0, m1 = i1 < d ? a[i1] : 0;
-            uint32_t r0 = 0, r1 = 0;
-            for (int j = 0; j < d; j++) {
-                const uint64_t y = a[j];
-                r0 += y < m0;
-                r1 += y < m1;
+            const int C = (d + 31) >> 5, sh = WARPS / C;
+            if (wid < C * sh) {
+                const int c = wid / sh, part = wid % sh;
+                const int i = c * 32 + lane;
+                const uint64_t m = i < d ? a[i] : 0;
+                const int j0 = part * d / sh, j1 = (part + 1) * d / sh;
+                uint32_t r = 0;
+                int j = j0;
+                for (; j + 4 <= j1; j += 4) {
+                    r += (a[j] < m) + (a[j + 1] < m);
+                    r += (a[j + 2] < m) + (a[j + 3] < m);
+                }
+                for (; j < j1; j++) r += a[j] < m;
+                if (i < d) {
+                    if (sh == 1) rank[i] = r;
+                    else atomicAdd(&rank[i], r);
+                }
             }
-            if (i0 < d) {
-                S.u.sl[m0 & (HT - 1)] = (uint16_t)r0;
-                tmpU[ls + r0] = (m0 >> LG_HT) + r_lo;
-            }
-            if (i1 < d) {
-                S.u.sl[m1 & (HT - 1)] = (uint16_t)r1;
-                tmpU[ls + r1] = (m1 >> LG_HT) + r_lo;
+            __syncthreads();
+            if (threadIdx.x < d) {
+                const uint64_t m = a[threadIdx.x];
+                const uint32_t r = rank[threadIdx.x];
+                S.u.sl[m & (HT - 1)] = (uint16_t)r;
+                tmpU[ls + r] = (m >> LG_HT) + r_lo;
             }
         } else {
             uint32_t *np = nullptr, *nq = nullptr;
