@@ -452,28 +452,40 @@ def run_e2e(args, s, sysd, dev):
     h_unique = torch.empty((n_unique, W), dtype=torch.int64).pin_memory()
     h_inverse = torch.empty(total, dtype=torch.int32 if total < 2 ** 31 else torch.int64).pin_memory()
     times = []
+    parts = []
 
     def one():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
         d = host.to(dev, non_blocking=True)
+        ev[1].record()
         off, od, oh, st = cusci.coupled(sysd, d, s.eps)
+        ev[2].record()
         u, inv, d_nu = cusci.dedup(od, n_bits, n_ones, sync=False)
+        ev[3].record()
         h_unique.copy_(u[:n_unique], non_blocking=True)
         h_inverse.copy_(inv, non_blocking=True)
+        ev[4].record()
         torch.cuda.current_stream().synchronize()
-        return int(od.shape[0])
+        return int(od.shape[0]), [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
 
     for _ in range(2):
         one()
     for _ in range(max(2, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        got = one()
+        got, ph = one()
         times.append(time.perf_counter() - t0)
+        parts.append(ph)
         assert got == total
     t = float(np.mean(times))
+    ph = np.mean(np.array(parts), axis=0)
     d2h = int(h_unique.numel() * 8 + h_inverse.numel() * h_inverse.element_size())
     return {"value": total / t, "unit": UNIT, "h2d_bytes_per_step": int(host.numel() * 8),
             "d2h_bytes_per_step": d2h, "ms_per_step": t * 1e3,
+            "phases_ms": {"h2d": float(ph[0]), "count+scan+fill": float(ph[1]),
+                          "dedup": float(ph[2]), "d2h": float(ph[3])},
+            "d2h_gbs": d2h / (float(ph[3]) * 1e-3) / 1e9 if ph[3] > 0 else None,
             "api": "cusci.coupled + cusci.dedup (host-pinned sources in; sorted distinct set "
                    "and reverse index out to pinned host memory)"}
 
@@ -567,21 +579,25 @@ def run_stream(args, dev):
         ys.append(time.perf_counter() - t0)
     plain_gbs = nbytes / min(ys) / 1e9
     del src
-    # peak pool use against the batch size, with and without the offload
+    # peak pool use against the batch size (offload on), beside the device
+    # memory the same pass needs un-staged: sources, counts and offsets, all
+    # coupled lists, the dedup workspace, the distinct set and the inverse
     curve = []
-    for be in (batch // 4, batch, batch * 4):
-        for offload in (True, False):
-            bufs = cusci.stream_buffers(sysd, s.dets, be, ucap, 0)
-            bufs["hd"], bufs["hh"] = buffers["hd"], buffers["hh"]  # pinned sinks reused
-            r = cusci.stream_gen_dedup(sysd, s.dets, s.eps, be, ucap, offload=offload,
-                                       buffers=bufs)
-            del bufs
-            curve.append({"batch_entries": be, "offload": offload,
-                          "pool_bytes": int(r[4]["pool_bytes"]),
-                          "pool_peak_bytes": int(r[4]["pool_peak"]),
-                          "batches": int(r[4]["batches"])})
-            del r
-            torch.cuda.empty_cache()
+    for be in (batch // 4, batch, batch * 4, batch * 16):
+        bufs = cusci.stream_buffers(sysd, s.dets, be, ucap, 0)
+        bufs["hd"], bufs["hh"] = buffers["hd"], buffers["hh"]  # pinned sinks reused
+        r = cusci.stream_gen_dedup(sysd, s.dets, s.eps, be, ucap, buffers=bufs)
+        del bufs
+        curve.append({"batch_entries": be, "pool_bytes": int(r[4]["pool_bytes"]),
+                      "pool_peak_bytes": int(r[4]["pool_peak"]), "batches": int(r[4]["batches"]),
+                      "ms": r[4]["batches_ms"] + r[4]["final_sort_ms"]})
+        del r
+        torch.cuda.empty_cache()
+    W = sysd.W
+    n_src, total_all, n_u = s.dets.shape[0], int(st["total"]), int(uniq.shape[0])
+    unstaged = (n_src * 8 * W + 2 * (n_src + 1) * 8 + total_all * (8 * W + 8)
+                + cusci.dedup_workspace(total_all, W, 2 * s.norb, s.n_alpha + s.n_beta)
+                + n_u * 8 * W + total_all * 4)
     # Stage-3 reverse index of the host-resident coupled set against the device
     # distinct set, streamed back in batches
     total_e = st["total"]
@@ -611,7 +627,9 @@ def run_stream(args, dev):
             "pool_peak_bytes": st["pool_peak"], "batch_region_bytes": 2 * batch * 24,
             "coupled_set_bytes": st["total"] * 24, "d2h_bytes": st["d2h_bytes"],
             "d2h_gbs": st["d2h_bytes"] / t / 1e9, "plain_pinned_d2h_gbs": plain_gbs,
-            "unique_capacity": ucap, "peak_vs_batch": curve,
+            "batches_ms": st["batches_ms"], "final_sort_ms": st["final_sort_ms"],
+            "unique_capacity": ucap, "peak_vs_batch": curve, "unstaged_peak_bytes": unstaged,
+            "pool_peak_vs_unstaged": st["pool_peak"] / unstaged,
             "reverse_index": rev,
             "workload": f"large: 120 spin orbitals (2 words), 10a+10b, {s.dets.shape[0]} sources, "
                         "eps 1e-6; host sources in, host coupled lists + device distinct set out; "

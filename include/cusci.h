@@ -281,8 +281,10 @@ cusci_status cusci_topk_update(const double *d_scores, const int64_t *d_ids, int
  * of host_capacity entries receiving the coupled lists in canonical order, or
  * both NULL to skip the offload.  d_unique: device [unique_capacity][W],
  * receives the sorted distinct targets of all batches; *h_n_unique their
- * number.  h_stats (nullable, host int64[4]): total entries, batches, peak pool
- * bytes used, bytes offloaded.  Synchronous (returns when everything landed).
+ * number.  h_stats (nullable, host int64[6]): total entries, batches, peak pool
+ * bytes used, bytes offloaded, microseconds spent up to the last batch's
+ * offload (counts, batches, hash inserts, copies) and in the final sort of the
+ * distinct keys.  Synchronous (returns when everything landed).
  * Errors: CUSCI_ERR_OOM (pool or sinks too small, or a source longer than a
  * batch), CUSCI_ERR_OVERFLOW (more distinct keys than unique_capacity),
  * CUSCI_ERR_TIMEOUT (a bounded wait in the hash set gave up),

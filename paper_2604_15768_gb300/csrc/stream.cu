@@ -16,6 +16,7 @@
 //  * finally the distinct keys are compacted out of the hash set and sorted
 //    with the library's de-duplication into the caller's output.
 
+#include <chrono>
 #include <stdlib.h>
 #include <string.h>
 
@@ -149,10 +150,24 @@ __global__ void rel_offsets(const int64_t *__restrict__ abs_off, int64_t n,
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// power of two holding unique_capacity keys at a load of at most 3/4
 uint64_t table_slots(int64_t unique_capacity) {
     uint64_t c = 1024;
-    while (c < (uint64_t)unique_capacity * 2) c <<= 1;
+    while (c < (uint64_t)unique_capacity + (uint64_t)unique_capacity / 3) c <<= 1;
     return c;
+}
+
+// Pool layout: [per-source arrays][control words][X], X reused by the two
+// phases.  Phase 1 (batches): the hash table at X, the two batch buffers
+// after it.  Phase 2 (final sort): the inverse and the sort workspace ("tail")
+// at X over the dead table, the compacted distinct keys after max(table, tail)
+// (never inside the table, which the compaction reads).
+size_t inv_bytes(int64_t unique_capacity) {
+    return unique_capacity < ((int64_t)1 << 31) ? 4 : 8;
+}
+
+size_t sort_tail(int64_t unique_capacity, size_t ws) {
+    return al((size_t)unique_capacity * inv_bytes(unique_capacity)) + al(ws);
 }
 
 }  // namespace
@@ -171,10 +186,10 @@ extern "C" cusci_status cusci_stream_pool_bytes(const cusci_system *sys, int64_t
     const size_t bat = 2 * (al((size_t)batch_entries * 8 * W) + al((size_t)batch_entries * 8));
     size_t ws = 0;
     cusci_dedup_workspace(unique_capacity, W, 2 * sys->norb, sys->n_alpha + sys->n_beta, &ws);
-    const size_t phase2 = al(ws) + al((size_t)unique_capacity * 8) +
-                          al((size_t)unique_capacity * 8 * W);
-    const size_t phase1 = bat + al(4096);
-    *bytes = tab + per_src + (phase1 > phase2 ? phase1 : phase2) + al(4096);
+    const size_t tail = sort_tail(unique_capacity, ws);
+    const size_t phase1 = tab + bat;
+    const size_t phase2 = (tail > tab ? tail : tab) + al((size_t)unique_capacity * 8 * W);
+    *bytes = per_src + al(4096) + (phase1 > phase2 ? phase1 : phase2);
     return CUSCI_OK;
 }
 
@@ -199,11 +214,12 @@ extern "C" cusci_status cusci_stream_gen_dedup(
     if ((uintptr_t)d_pool & 255u) return fail(CUSCI_ERR_INVALID, "stream: pool not 256-aligned");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
+    const auto t_start = std::chrono::steady_clock::now();
 
     // carve the pool
     unsigned char *p = (unsigned char *)d_pool;
     const uint64_t slots = table_slots(unique_capacity);
-    uint64_t *tab = (uint64_t *)p; p += al(slots * 8 * W);
+    const size_t tab_bytes = al(slots * 8 * W);
     int64_t *d_counts = (int64_t *)p; p += al((size_t)(n + 1) * 8);
     int64_t *d_off = (int64_t *)p; p += al((size_t)(n + 1) * 8);
     int64_t *d_boff = (int64_t *)p; p += al((size_t)(n + 1) * 8);
@@ -211,7 +227,9 @@ extern "C" cusci_status cusci_stream_gen_dedup(
     unsigned char *phase = p;
     unsigned long long *d_ctr = (unsigned long long *)phase;   // [0] new keys, [1] compaction
     int32_t *d_status = (int32_t *)(phase + 64);
-    unsigned char *bat = phase + al(4096);
+    unsigned char *X = phase + al(4096);
+    uint64_t *tab = (uint64_t *)X;
+    unsigned char *bat = X + tab_bytes;
     uint64_t *bd[2];
     double *bh[2];
     bd[0] = (uint64_t *)bat; bat += al((size_t)batch_entries * 8 * W);
@@ -253,6 +271,9 @@ extern "C" cusci_status cusci_stream_gen_dedup(
         return fail(CUSCI_ERR_OOM, "stream: host sinks hold %lld entries, need %lld",
                     (long long)host_capacity, (long long)total);
 
+    // all offsets to the device once (batches take batch-relative views of them)
+    e = cudaMemcpyAsync(d_boff, h_offsets, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "stream: offsets");
     cudaStream_t cp;
     e = cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "stream: copy stream");
@@ -275,11 +296,8 @@ extern "C" cusci_status cusci_stream_gen_dedup(
             e = cudaStreamWaitEvent(st, copied[buf], 0);
             if (e != cudaSuccess) { rc = cuda_fail(e, "stream: wait"); break; }
         }
-        // batch-relative offsets (h_offsets is final, so the pageable copy may overlap)
-        e = cudaMemcpyAsync(d_boff, h_offsets + s0, (size_t)(s1 - s0 + 1) * 8,
-                            cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "stream: offsets"); break; }
-        rel_offsets<<<(int)((s1 - s0 + 256) / 256), 256, 0, st>>>(d_boff, s1 - s0 + 1, d_off);
+        // batch-relative offsets from the device copy of all offsets
+        rel_offsets<<<(int)((s1 - s0 + 256) / 256), 256, 0, st>>>(d_boff + s0, s1 - s0 + 1, d_off);
         note_launches(1);
         rc = cusci_gen_coupled(sys, d_src + s0 * W, s1 - s0, eps, d_off, bd[buf], bh[buf],
                                d_status, stream);
@@ -336,12 +354,15 @@ extern "C" cusci_status cusci_stream_gen_dedup(
         return fail(CUSCI_ERR_OVERFLOW, "stream: %llu distinct keys > capacity %lld", h_new,
                     (long long)unique_capacity);
     const int64_t nu = (int64_t)h_new;
-    unsigned char *q = phase + al(4096);  // batch region is free now
+    const auto t_batches = std::chrono::steady_clock::now();
+    // phase 2: inverse and sort workspace over the table, compacted keys after
     size_t ws = 0;
     cusci_dedup_workspace(nu > 0 ? nu : 1, W, 2 * sys->norb, N1, &ws);
-    uint64_t *raw = (uint64_t *)q; q += al((size_t)unique_capacity * 8 * W);
-    uint32_t *inv = (uint32_t *)q; q += al((size_t)unique_capacity * 8);
-    void *dws = q; q += al(ws);
+    const size_t tail = sort_tail(unique_capacity, ws);
+    void *inv = X;
+    void *dws = X + al((size_t)unique_capacity * inv_bytes(unique_capacity));
+    uint64_t *raw = (uint64_t *)(X + (tail > tab_bytes ? tail : tab_bytes));
+    const unsigned char *q = (const unsigned char *)raw + al((size_t)unique_capacity * 8 * W);
     const size_t peak2 = (size_t)(q - (unsigned char *)d_pool);
     if (peak2 > pool_bytes) return fail(CUSCI_ERR_OOM, "stream: pool too small for the final sort");
     int cb = (int)((slots + HT - 1) / HT);
@@ -364,6 +385,9 @@ extern "C" cusci_status cusci_stream_gen_dedup(
         h_stats[1] = nbatch;
         h_stats[2] = (int64_t)(peak1 > peak2 ? peak1 : peak2);
         h_stats[3] = offload ? total * (8 * W + 8) : 0;
+        const auto t_end = std::chrono::steady_clock::now();
+        h_stats[4] = std::chrono::duration_cast<std::chrono::microseconds>(t_batches - t_start).count();
+        h_stats[5] = std::chrono::duration_cast<std::chrono::microseconds>(t_end - t_batches).count();
     }
     return CUSCI_OK;
 }

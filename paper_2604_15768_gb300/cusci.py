@@ -343,7 +343,7 @@ def stream_gen_dedup(sys: System, dets: np.ndarray, eps: float, batch_entries: i
     hh = buffers["hh"] if offload else None
     cap = 0 if hd is None else hd.shape[0]
     nu = ctypes.c_int64(0)
-    stats = np.zeros(4, dtype=np.int64)
+    stats = np.zeros(6, dtype=np.int64)
     _check(load().cusci_stream_gen_dedup(
         sys.handle, ctypes.c_void_p(h_src.data_ptr()), n, float(eps), _ptr(pool), pool.numel(),
         int(batch_entries), offsets.ctypes.data_as(_P), _ptr(hd), _ptr(hh), cap, _ptr(uniq),
@@ -355,6 +355,8 @@ def stream_gen_dedup(sys: System, dets: np.ndarray, eps: float, batch_entries: i
     return offsets, out_d, out_h, uniq[:nu.value], {"total": int(stats[0]), "batches": int(stats[1]),
                                                      "pool_peak": int(stats[2]),
                                                      "d2h_bytes": int(stats[3]),
+                                                     "batches_ms": stats[4] / 1e3,
+                                                     "final_sort_ms": stats[5] / 1e3,
                                                      "pool_bytes": int(pool.numel())}
 
 
