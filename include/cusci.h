@@ -233,11 +233,49 @@ cusci_status cusci_local_energy_bwd(const int64_t *d_offsets, int64_t n, const d
  * d_splitters (device [P-1][W]).  d_bounds (device int64 [P][P+1]) receives the
  * cuts: rank q's share of run r is rows [bounds[r][q], bounds[r][q+1]), the keys
  * k with splitter[q-1] < k <= splitter[q].  P * S * W must not exceed 16384
- * (next power of two).  Step 3 (exchange and final merge) is data movement plus
- * cusci_dedup per rank. */
+ * (next power of two).  Step 3 (exchange and final merge) is
+ * cusci_partition_exchange, one cusci_dedup and cusci_partition_split. */
 cusci_status cusci_partition_plan(const uint64_t *d_keys, int W, const int64_t *d_run_offsets,
                                   int P, int S, uint64_t *d_splitters, int64_t *d_bounds,
                                   void *stream);
+/* Step 1 of the same de-duplication for P ranks on one GPU (Sec. 4.1.1): rank r
+ * owns entries [d_entry_offsets[r], d_entry_offsets[r+1]) (device int64[P+1],
+ * non-decreasing, [0] = 0, [P] = total) of d_keys (device [total][W], keys
+ * below 2^n_bits).  d_joint (device [total][W]) receives every key with its
+ * owner rank written into bits [n_bits, n_bits + ceil(log2 P)), so that one
+ * cusci_dedup of d_joint (n_bits + ceil(log2 P) bits, n_ones = -1) yields all
+ * ranks' locally sorted distinct runs, in rank order.  A key with a bit at or
+ * above n_bits sets *d_status (nullable) to CUSCI_ERR_INVALID.  1 <= P <= 1024;
+ * CUSCI_ERR_UNSUPPORTED when n_bits + ceil(log2 P) > 64 W.  Asynchronous. */
+cusci_status cusci_rank_join(const uint64_t *d_keys, int W, int64_t total,
+                             const int64_t *d_entry_offsets, int P, int n_bits,
+                             uint64_t *d_joint, int32_t *d_status, void *stream);
+/* The runs of Step 1 out of the sorted distinct joined keys: d_runs (device
+ * [capacity][W]) receives the first *d_n_unique keys (a device count, e.g.
+ * from cusci_dedup) with the rank bits cleared; d_run_offsets (device
+ * int64[P+1]) the start of every rank's run ([P] = *d_n_unique).  Same P and
+ * n_bits as cusci_rank_join.  Asynchronous. */
+cusci_status cusci_rank_runs(const uint64_t *d_joint_unique, int W, const int64_t *d_n_unique,
+                             int64_t capacity, int P, int n_bits, uint64_t *d_runs,
+                             int64_t *d_run_offsets, void *stream);
+/* Step 3's all-to-all on one GPU (Sec. 4.1.1, Fig. 3): rank q receives, in
+ * rank order r = 0..P-1, rows [d_bounds[r][q], d_bounds[r][q+1]) of d_runs
+ * (the cuts of cusci_partition_plan, device int64 [P][P+1]).  Rank q's rows are
+ * written to d_recv (device, rows >= the runs' total) from row
+ * d_recv_offsets[q]; d_recv_offsets (device int64[P+1]) is written here,
+ * [P] = rows received in all.  One block per (q, r) segment.  Asynchronous. */
+cusci_status cusci_partition_exchange(const uint64_t *d_runs, int W, int P,
+                                      const int64_t *d_bounds, uint64_t *d_recv,
+                                      int64_t *d_recv_offsets, void *stream);
+/* Final partitions: the ranks' key ranges are disjoint, so one cusci_dedup of
+ * all received rows is every rank's final sort + unique at once; this cuts its
+ * output d_unique (device [*][W], *d_n_unique rows) at the P-1 splitters:
+ * d_part_offsets (device int64[P+1]) receives for q = 1..P-1 the number of
+ * distinct keys <= splitter[q-1], [0] = 0 and [P] = *d_n_unique.
+ * Asynchronous. */
+cusci_status cusci_partition_split(const uint64_t *d_unique, int W, const int64_t *d_n_unique,
+                                   const uint64_t *d_splitters, int P, int64_t *d_part_offsets,
+                                   void *stream);
 
 /* ------------------------------------------------------------------ reverse index
  * Just-in-time reverse index (Stage 3 of Sec. 3, Sec. 4.3.4): d_inverse[k] =

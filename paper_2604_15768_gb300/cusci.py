@@ -74,6 +74,10 @@ _PROTOS = {
     "cusci_local_energy_bwd": (_I, [_P, _I64, _P, _P, _I, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ,
                                     _P]),
     "cusci_partition_plan": (_I, [_P, _I, _P, _I, _I, _P, _P, _P]),
+    "cusci_rank_join": (_I, [_P, _I, _I64, _P, _I, _I, _P, _P, _P]),
+    "cusci_rank_runs": (_I, [_P, _I, _P, _I64, _I, _I, _P, _P, _P]),
+    "cusci_partition_exchange": (_I, [_P, _I, _I, _P, _P, _P, _P]),
+    "cusci_partition_split": (_I, [_P, _I, _P, _P, _I, _P, _P]),
     "cusci_reverse_index": (_I, [_P, _I64, _I, _P, _I64, _P, _I, _P, _P]),
     "cusci_topk_workspace": (_I, [_I64, _I64, ctypes.POINTER(_SZ)]),
     "cusci_topk_update": (_I, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, _P, _P]),
@@ -538,50 +542,61 @@ def partition_plan(runs: torch.Tensor, run_offsets: torch.Tensor, P: int, S: int
 
 
 def virtual_rank_dedup(keys: torch.Tensor, entry_offsets, P: int, S: int, n_bits: int,
-                       n_ones: int):
+                       n_ones: int, stream=None):
     """The paper's distributed de-duplication (Sec. 4.1.1) over P virtual ranks on
-    one GPU.  Rank r owns the entries [entry_offsets[r], entry_offsets[r+1]) of
-    ``keys``.  Step 1: local sort + unique and regular sampling; Step 2: splitters
-    and cuts; Step 3: all-to-all (device copies) and a final sort + unique per
-    rank.  Returns (list of per-rank distinct partitions, stats dict)."""
+    one GPU, as a device pipeline with one host read-back at the end.  Rank r
+    owns the entries [entry_offsets[r], entry_offsets[r+1]) of ``keys``.
+    Step 1: every rank's local sort + unique, all ranks in one dedup of the
+    rank-joined keys; Step 2: samples, splitters and cuts; Step 3: the
+    all-to-all as one device gather and every rank's final sort + unique as one
+    dedup of the received rows, cut at the splitters.  Returns (list of per-rank
+    distinct partitions, stats dict, splitters, cuts, runs, run offsets)."""
+    keys = _dev(keys, torch.int64, "keys")
     dev = keys.device
-    W = keys.shape[1]
-    eo = [int(x) for x in entry_offsets]
-    local = []
-    for r in range(P):
-        a, b = eo[r], eo[r + 1]
-        if b > a:
-            u, _, nu = dedup(keys[a:b], n_bits, n_ones)
-            local.append(u[:nu])
-        else:
-            local.append(torch.empty((0, W), dtype=torch.int64, device=dev))
-    run_off = torch.tensor(np.concatenate([[0], np.cumsum([x.shape[0] for x in local])]),
-                           dtype=torch.int64, device=dev)
-    runs = torch.cat(local) if sum(x.shape[0] for x in local) else torch.empty((1, W),
-                                                                               dtype=torch.int64,
-                                                                               device=dev)
-    spl, bounds = partition_plan(runs, run_off, P, S)
-    bh = bounds.cpu().numpy()
-    parts, received = [], []
-    for q in range(P):
-        pieces = [runs[bh[r, q]:bh[r, q + 1]] for r in range(P) if bh[r, q + 1] > bh[r, q]]
-        recv = torch.cat(pieces) if pieces else torch.empty((0, W), dtype=torch.int64, device=dev)
-        received.append(int(recv.shape[0]))
-        if recv.shape[0]:
-            u, _, nu = dedup(recv, n_bits, n_ones)
-            parts.append(u[:nu])
-        else:
-            parts.append(recv)
-    uniq = np.array([x.shape[0] for x in parts], dtype=np.float64)
-    recv = np.array(received, dtype=np.float64)
+    total, W = keys.shape
+    eo = torch.as_tensor(np.asarray(entry_offsets, dtype=np.int64)).to(dev)
+    lib = load()
+    lg = (P - 1).bit_length()
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    joint = torch.empty((max(total, 1), W), dtype=torch.int64, device=dev)
+    _check(lib.cusci_rank_join(_ptr(keys), W, total, _ptr(eo), int(P), int(n_bits), _ptr(joint),
+                               _ptr(status), _stream(stream)), "cusci_rank_join")
+    ju, _, ju_n = dedup(joint[:total], n_bits + lg, -1, status=status, stream=stream, sync=False)
+    runs = torch.empty((max(total, 1), W), dtype=torch.int64, device=dev)
+    run_off = torch.empty(P + 1, dtype=torch.int64, device=dev)
+    _check(lib.cusci_rank_runs(_ptr(ju), W, _ptr(ju_n), total, int(P), int(n_bits), _ptr(runs),
+                               _ptr(run_off), _stream(stream)), "cusci_rank_runs")
+    del joint, ju
+    spl, bounds = partition_plan(runs, run_off, P, S, stream=stream)
+    recv = torch.empty((max(total, 1), W), dtype=torch.int64, device=dev)
+    recv_off = torch.empty(P + 1, dtype=torch.int64, device=dev)
+    _check(lib.cusci_partition_exchange(_ptr(runs), W, int(P), _ptr(bounds), _ptr(recv),
+                                        _ptr(recv_off), _stream(stream)),
+           "cusci_partition_exchange")
+    n_recv = int(recv_off[-1].item())                  # the one host read-back
+    fu, _, fu_n = dedup(recv[:n_recv], n_bits, n_ones, status=status, stream=stream, sync=False)
+    part_off = torch.empty(P + 1, dtype=torch.int64, device=dev)
+    spl_full = spl if P > 1 else torch.zeros((1, W), dtype=torch.int64, device=dev)
+    _check(lib.cusci_partition_split(_ptr(fu), W, _ptr(fu_n), _ptr(spl_full), int(P),
+                                     _ptr(part_off), _stream(stream)), "cusci_partition_split")
+    st = int(status.item())
+    if st != 0:
+        raise CusciError(f"virtual_rank_dedup: device status {st}")
+    po = part_off.cpu().numpy()
+    ro = run_off.cpu().numpy()
+    rv = recv_off.cpu().numpy()
+    parts = [fu[po[q]:po[q + 1]] for q in range(P)]
+    recv_n = np.diff(rv).astype(np.float64)
+    uniq = np.diff(po).astype(np.float64)
     # the paper's load-balance metric: items per rank after the exchange
-    stats = {"P": P, "S": S, "received": received, "unique": [int(x) for x in uniq],
-             "max_over_min": float(recv.max() / max(recv.min(), 1.0)),
-             "cv": float(recv.std() / recv.mean()) if recv.mean() > 0 else 0.0,
+    stats = {"P": P, "S": S, "received": [int(x) for x in recv_n],
+             "unique": [int(x) for x in uniq],
+             "max_over_min": float(recv_n.max() / max(recv_n.min(), 1.0)),
+             "cv": float(recv_n.std() / recv_n.mean()) if recv_n.mean() > 0 else 0.0,
              "unique_max_over_min": float(uniq.max() / max(uniq.min(), 1.0)),
              "unique_cv": float(uniq.std() / uniq.mean()) if uniq.mean() > 0 else 0.0,
-             "local_distinct": [int(x.shape[0]) for x in local]}
-    return parts, stats, spl, bounds, runs, run_off
+             "local_distinct": [int(x) for x in np.diff(ro)]}
+    return parts, stats, spl, bounds, runs[:int(ro[-1])], run_off
 
 
 class LocalEnergy(torch.autograd.Function):
