@@ -49,6 +49,11 @@ WORKLOADS = {
 }
 
 TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 117.35, "cusci_gen_coupled (fill_kernel)": 15.94}
+# the same capture per phase of the dedup call (the phase names of
+# cusci_dedup_phase_name; scans and tiny launches folded into their phase)
+DEDUP_KERNEL_B_PER_ENTRY = {"sample+splitters": 0.91, "hist1": 9.95, "scatter1": 25.12,
+                            "level2": 32.76, "leaf_dedup": 14.87, "compact_unique": 5.00,
+                            "unscatter2": 16.81, "unscatter1": 11.91}
 UNIT = "entries/s"
 
 
@@ -247,6 +252,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    cusci.set_kernel_timing(True)   # per-phase events inside the dedup calls of the timed steps
     wall0 = time.perf_counter()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -259,6 +265,8 @@ def run_ours(args):
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = cusci.kernel_launches() - l0
+    phase_ms, phase_calls = cusci.dedup_phase_ms()
+    cusci.set_kernel_timing(False)
     for m in per_step:
         t_count.append(m[0].elapsed_time(m[1]))
         t_gen.append(m[1].elapsed_time(m[2]))
@@ -282,6 +290,20 @@ def run_ours(args):
     dominant = "cusci_dedup" if dedup_ms >= gen_ms else "cusci_gen_coupled (fill_kernel)"
     tpe = TRAFFIC_B_PER_ENTRY.get(dominant) if args.workload == "mid" else None
     traffic = None if tpe is None else tpe * total
+    # the dedup call's kernels: mean CUDA-event time per call over the timed
+    # steps, DRAM traffic per launch from the capture, achieved DRAM GB/s
+    hbm_peak_k, _ = _peaks()
+    dedup_kernels = {}
+    for name, tot_ms in phase_ms.items():
+        if phase_calls == 0:
+            break
+        k_ms = tot_ms / phase_calls
+        bpe = DEDUP_KERNEL_B_PER_ENTRY.get(name) if args.workload == "mid" else None
+        rec = {"ms": k_ms}
+        if bpe is not None and k_ms > 0:
+            gbs = bpe * total / (k_ms * 1e-3) / 1e9
+            rec.update({"dram_b_per_entry": bpe, "dram_gbs": gbs, "frac_of_hbm": gbs / hbm_peak_k})
+        dedup_kernels[name] = rec
     dom_gbs, dom_bytes, dom_ms = ((dedup_gbs, dedup_bytes, dedup_ms) if dedup_ms >= gen_ms
                                   else (gen_gbs, gen_bytes, gen_ms))
 
@@ -410,6 +432,7 @@ def run_ours(args):
                               "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
                               "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak},
             "phases_ms": {"count+scan": count_ms, "gen": gen_ms, "dedup": dedup_ms},
+            "dedup_kernels": dedup_kernels,
             "phases_gbs": {"gen": gen_gbs, "dedup": dedup_gbs},
             "gpu_launches": launches,
             "clocks": clk.summary(),

@@ -74,6 +74,20 @@ const char *cusci_version(void);
 /* Number of kernels the library has launched in this process so far (host-side
  * count of successful launches, all devices and streams). */
 uint64_t cusci_kernel_launches(void);
+/* Per-kernel timing of the sample-sort de-duplication (diagnostics; the
+ * regular-sampling partition of Sec. 4.1.1).  cusci_set_kernel_timing(1)
+ * resets the record and makes every later cusci_dedup call on that path (up to
+ * 64 calls, on the current device) record a CUDA event on its own stream
+ * before its first kernel and after each of its phases; 0 stops recording.
+ * cusci_dedup_phase_ms waits for the recorded events and writes, for phase
+ * i < min(max, number of phases), the summed milliseconds of all recorded
+ * calls to h_ms[i] (host array); *h_calls (nullable) receives the number of
+ * calls summed.  Returns the number of phases written.  Phase names come from
+ * cusci_dedup_phase_name(i) (static strings; NULL out of range).  Timing adds
+ * no synchronisation to the calls themselves. */
+cusci_status cusci_set_kernel_timing(int on);
+int cusci_dedup_phase_ms(double *h_ms, int max, int *h_calls);
+const char *cusci_dedup_phase_name(int i);
 
 /* ------------------------------------------------------------------ system
  * Builds the device-side integral tables of one molecular system (the

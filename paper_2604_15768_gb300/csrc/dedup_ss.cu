@@ -37,6 +37,8 @@
 
 #include <string.h>
 
+#include <mutex>
+
 #include "radix.cuh"
 
 namespace cusci {
@@ -1115,6 +1117,38 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Optional per-kernel timing (diagnostics): while enabled, every call records
+// a CUDA event on its own stream before its first kernel and after each
+// phase; the elapsed times of up to TIMED_CALLS calls are summed on query.
+constexpr int NPHASE = 8;
+constexpr int TIMED_CALLS = 64;
+const char *const PHASE_NAME[NPHASE] = {"sample+splitters", "hist1",      "scatter1",
+                                        "level2",           "leaf_dedup", "compact_unique",
+                                        "unscatter2",       "unscatter1"};
+struct PhaseTimer {
+    std::mutex mu;
+    bool on = false;
+    bool created = false;
+    int dev = -1;
+    int calls = 0;
+    cudaEvent_t ev[TIMED_CALLS][NPHASE + 1];
+};
+PhaseTimer g_timer;
+
+// the event row of this call, or nullptr when timing is off or full
+cudaEvent_t *timer_row() {
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!g_timer.on || !g_timer.created || dev != g_timer.dev || g_timer.calls >= TIMED_CALLS)
+        return nullptr;
+    return g_timer.ev[g_timer.calls++];
+}
+
+inline void mark(cudaEvent_t *row, int i, cudaStream_t st) {
+    if (row) cudaEventRecord(row[i], st);
+}
+
 template <int W>
 cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_t *unique,
                  void *inverse, int index_bytes, int64_t *d_n_unique, int32_t *status,
@@ -1142,6 +1176,8 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
     int64_t *ubase = (int64_t *)(ws + p.o_ubase);
     const int sms = sm_count();
     int launches = 0;
+    cudaEvent_t *tr = timer_row();
+    mark(tr, 0, st);
 
     build_bt<<<1, 32, 0, st>>>(bt, p.n_bits, p.kcols);
     launches++;
@@ -1187,8 +1223,10 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
         if (rc0 == CUSCI_OK) rc0 = allow_smem((const void *)leaf_dedup, sizeof(LeafSmem), what);
         if (rc0 != CUSCI_OK) return rc0;
     }
+    mark(tr, 1, st);
     hist1<W><<<p.G, T, sm_h1, st>>>(keys, p.N, p.per_cta, p.mode, p.n_bits, p.n_ones, p.kcols, bt,
                                     LS, p.B1, p.log2B1, T1, krange, bid1, H1, status);
+    mark(tr, 2, st);
     scatter1<W><<<p.G, T, sm_x1, st>>>(keys, p.N, p.per_cta, p.mode, p.n_bits, p.kcols, bt, bid1,
                                        p.B1, H1, base1, K1, dest1);
     cusci_status rc = CUSCI_OK;
@@ -1197,23 +1235,29 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
     rc = exclusive_scan_i64(kbase, p.B1, kbase, scanws, st);
     if (rc != CUSCI_OK) return rc;
     launches += 3;
+    mark(tr, 3, st);
     // level 2
     level2<<<p.B1, T, 0, st>>>(K1, p.N, base1, H1, p.G, p.B1, kbase, LS, p.NL, bid2, K2, dest2,
                                leafst);
     launches++;
+    mark(tr, 4, st);
     // leaves
     uint32_t *pay = (uint32_t *)(ws + p.o_pay);
     leaf_dedup<<<sms * 4, T, sizeof(LeafSmem), st>>>(K2, K1, pay, p.N, p.NL, leafst, U2, tmpU, ucnt);
     launches++;
+    mark(tr, 5, st);
     rc = exclusive_scan_i64(ucnt, p.NL, ubase, scanws, st);
     if (rc != CUSCI_OK) return rc;
     compact_unique<W><<<sms * 4, T, 0, st>>>(tmpU, leafst, ucnt, ubase, p.NL, p.mode, p.n_bits,
                                              p.n_ones, p.kcols, bt, unique, d_n_unique);
+    mark(tr, 6, st);
     unscatter2<<<p.B1, T, 0, st>>>(base1, H1, p.G, p.B1, bid2, dest2, U2, ubase);
+    mark(tr, 7, st);
     if (index_bytes == 4)
         unscatter1<int32_t><<<sms * 4, 256, 0, st>>>(dest1, dest2, p.N, (int32_t *)inverse);
     else
         unscatter1<int64_t><<<sms * 4, 256, 0, st>>>(dest1, dest2, p.N, (int64_t *)inverse);
+    mark(tr, 8, st);
     launches += 3;
     CUSCI_LAUNCHED(launches, "sample-sort dedup");
     return CUSCI_OK;
@@ -1249,3 +1293,59 @@ cusci_status ss_dedup(const uint64_t *keys, int64_t N, int W, int n_bits, int n_
 }
 
 }  // namespace cusci
+
+using namespace cusci;
+
+extern "C" cusci_status cusci_set_kernel_timing(int on) {
+    std::lock_guard<std::mutex> lk(ss::g_timer.mu);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cusci_set_kernel_timing: device");
+    if (on && (!ss::g_timer.created || ss::g_timer.dev != dev)) {
+        if (ss::g_timer.created) {
+            for (int c = 0; c < ss::TIMED_CALLS; c++)
+                for (int i = 0; i <= ss::NPHASE; i++) cudaEventDestroy(ss::g_timer.ev[c][i]);
+            ss::g_timer.created = false;
+        }
+        for (int c = 0; c < ss::TIMED_CALLS; c++)
+            for (int i = 0; i <= ss::NPHASE; i++) {
+                e = cudaEventCreate(&ss::g_timer.ev[c][i]);
+                if (e != cudaSuccess) return cuda_fail(e, "cusci_set_kernel_timing: events");
+            }
+        ss::g_timer.created = true;
+        ss::g_timer.dev = dev;
+    }
+    ss::g_timer.on = on != 0;
+    if (on) ss::g_timer.calls = 0;  // stopping keeps the record for the query
+    return CUSCI_OK;
+}
+
+extern "C" const char *cusci_dedup_phase_name(int i) {
+    return i >= 0 && i < ss::NPHASE ? ss::PHASE_NAME[i] : nullptr;
+}
+
+extern "C" int cusci_dedup_phase_ms(double *h_ms, int max, int *h_calls) {
+    std::lock_guard<std::mutex> lk(ss::g_timer.mu);
+    const int n = max < ss::NPHASE ? max : ss::NPHASE;
+    for (int i = 0; i < n; i++) h_ms[i] = 0.0;
+    int used = 0;
+    for (int c = 0; ss::g_timer.created && c < ss::g_timer.calls; c++) {
+        if (cudaEventSynchronize(ss::g_timer.ev[c][ss::NPHASE]) != cudaSuccess) {
+            cudaGetLastError();  // a call that stopped early recorded no end event
+            continue;
+        }
+        float t[ss::NPHASE];
+        bool ok = true;
+        for (int i = 0; i < ss::NPHASE && ok; i++)
+            ok = cudaEventElapsedTime(&t[i], ss::g_timer.ev[c][i], ss::g_timer.ev[c][i + 1]) ==
+                 cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            continue;
+        }
+        for (int i = 0; i < n; i++) h_ms[i] += t[i];
+        used++;
+    }
+    if (h_calls) *h_calls = used;
+    return n;
+}

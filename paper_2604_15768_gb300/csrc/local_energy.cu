@@ -107,7 +107,10 @@ __device__ __forceinline__ void fx_add(unsigned long long *a, double c) {
     const unsigned long long lo = __double2ull_rz(__dmul_rn(frac, 18446744073709551616.0));
     const unsigned long long old = atomicAdd(a, lo);
     const unsigned long long carry = old + lo < old ? 1ull : 0ull;
-    atomicAdd(a + 1, (unsigned long long)ip + carry);
+    // the high word changes only by ip + carry: zero for a term in [0, 1)
+    // without a carry, and for a term in [-1, 0) whose low word wrapped
+    const unsigned long long hi = (unsigned long long)ip + carry;
+    if (hi != 0ull) atomicAdd(a + 1, hi);
 }
 
 template <typename IDX>

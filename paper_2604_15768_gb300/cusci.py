@@ -43,6 +43,9 @@ _PROTOS = {
     "cusci_last_error": (ctypes.c_char_p, []),
     "cusci_version": (ctypes.c_char_p, []),
     "cusci_kernel_launches": (ctypes.c_uint64, []),
+    "cusci_set_kernel_timing": (_I, [_I]),
+    "cusci_dedup_phase_ms": (_I, [_P, _I, _P]),
+    "cusci_dedup_phase_name": (ctypes.c_char_p, [_I]),
     "cusci_system_create": (_I, [_I, _I, _I, _P, _P, _D, ctypes.POINTER(_P)]),
     "cusci_system_destroy": (None, [_P]),
     "cusci_system_words": (_I, [_P]),
@@ -111,6 +114,21 @@ def load(path: str | None = None):
 def kernel_launches() -> int:
     """Kernels launched by libcusci in this process so far."""
     return int(load().cusci_kernel_launches())
+
+
+def set_kernel_timing(on: bool):
+    """Start (resetting the record) or stop per-phase event timing of the
+    sample-sort de-duplication."""
+    _check(load().cusci_set_kernel_timing(1 if on else 0), "cusci_set_kernel_timing")
+
+
+def dedup_phase_ms():
+    """(dict phase name -> summed ms, number of calls) of the recorded calls."""
+    lib = load()
+    ms = np.zeros(16, dtype=np.float64)
+    calls = ctypes.c_int(0)
+    n = lib.cusci_dedup_phase_ms(ms.ctypes.data_as(_P), 16, ctypes.byref(calls))
+    return {lib.cusci_dedup_phase_name(i).decode(): float(ms[i]) for i in range(n)}, calls.value
 
 
 def _check(rc: int, where: str):

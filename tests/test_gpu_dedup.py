@@ -212,3 +212,21 @@ def test_sample_sort_hash_path_limits_vs_oracle():
     top = np.uint64(0xFFFFFFFFFFFFFFFF) - rng.integers(0, 1 << 30, size=n).astype(np.uint64)
     top[rng.choice(n, 20_000, replace=False)] = np.uint64(0xFFFFFFFFFFFFFFFF)
     compare(top.reshape(-1, 1), 64, -1)
+
+
+def test_kernel_timing_records_every_phase():
+    """Per-phase event timing of the sample-sort path: one call while enabled
+    gives one recorded call with a positive time for every phase, calls after
+    it is disabled add nothing, and the results are unchanged."""
+    rng = np.random.default_rng(30)
+    keys = rng.integers(0, 1 << 36, size=4_400_000).astype(np.uint64).reshape(-1, 1)
+    cusci.set_kernel_timing(True)
+    compare(keys, 36, -1)
+    ms, calls = cusci.dedup_phase_ms()
+    cusci.set_kernel_timing(False)
+    gpu_dedup(keys, 36, -1)
+    ms2, calls2 = cusci.dedup_phase_ms()
+    assert calls == 1 and calls2 == 1
+    assert list(ms) == ["sample+splitters", "hist1", "scatter1", "level2", "leaf_dedup",
+                        "compact_unique", "unscatter2", "unscatter1"]
+    assert all(v > 0 for v in ms.values())
