@@ -22,7 +22,9 @@
 //  3. Each leaf is de-duplicated in shared memory: every entry is inserted
 //     into an open-addressing hash table (its slot kept), the few distinct
 //     keys are compacted, packed as (key - leaf_min) << 12 | slot and ordered
-//     (rank counting for up to 256 of them, 8-bit LSD passes otherwise), and
+//     (rank counting for up to 32 of them; else one counting pass on the top
+//     8 bits of their range and counting inside each bucket; 8-bit LSD
+//     passes when a bucket is too full), and
 //     every entry reads its local unique id back through its slot.  Leaves
 //     that are too large or too diverse are LSD-sorted in global memory with
 //     their positions in a separate array and walked for run heads.
@@ -38,6 +40,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "radix.cuh"
 
@@ -52,6 +55,7 @@ constexpr int T = 256;
 constexpr int WARPS = T / 32;
 constexpr int B2 = 256;
 constexpr int LOG2_B2 = 8;
+using Bid2 = std::conditional<(B2 <= 256), uint8_t, uint16_t>::type;  // leaf id in a bucket
 constexpr int OVS = 4;
 constexpr int LEAF_AVG = 1600;
 constexpr int MAX_B1 = 4096;
@@ -150,7 +154,7 @@ Plan make_plan(int64_t N, int W, int n_bits, int n_ones, int mode, int key_bits)
     p.o_bid1 = o; o = al(o + N * 2);
     p.o_K1 = o; o = al(o + N * 8);
     p.o_dest1 = o; o = al(o + N * 4);
-    p.o_bid2 = o; o = al(o + N * 1);
+    p.o_bid2 = o; o = al(o + N * sizeof(Bid2));
     p.o_K2 = o; o = al(o + N * 8);
     p.o_dest2 = o; o = al(o + N * 4);
     p.o_U2 = o; o = al(o + N * 4);
@@ -519,7 +523,7 @@ __global__ void __launch_bounds__(T)
 __global__ void __launch_bounds__(T)
     level2(const uint64_t *__restrict__ K1, int64_t N, const int64_t *__restrict__ base1,
            const uint32_t *__restrict__ H1, int G, int B1, const int64_t *__restrict__ kbase,
-           const uint64_t *__restrict__ LS, int64_t NL, uint8_t *__restrict__ bid2,
+           const uint64_t *__restrict__ LS, int64_t NL, Bid2 *__restrict__ bid2,
            uint64_t *__restrict__ K2, uint32_t *__restrict__ dest2,
            int64_t *__restrict__ leaf_start) {
     __shared__ uint64_t L[B2];
@@ -558,7 +562,7 @@ __global__ void __launch_bounds__(T)
                 if (k < len) {
                     const int c = cell_of(x[u], blo, bshift, LG_CELLS2);
                     const int b = count_less_in(L, T2[c], T2[c + 1], x[u]);
-                    bid2[sb + k] = (uint8_t)b;
+                    bid2[sb + k] = (Bid2)b;
                     atomicAdd(&h[b], 1u);
                 }
             }
@@ -620,14 +624,16 @@ __global__ void __launch_bounds__(T)
 // an open-addressing hash table in shared memory (one probe sequence per entry,
 // no sort of the entries themselves): the distinct keys are then compacted,
 // packed as (key - leaf_min) << LG_HT | slot and ordered -- by counting ranks
-// when there are few of them, by LSD radix passes otherwise -- and every entry
-// reads its rank back through its slot.  Leaves with more entries, more than
-// HASH_D distinct keys, a key equal to the empty marker or a key range too
-// wide to pack are LSD-sorted in global memory with their positions alongside.
+// when there are few of them, else by one counting pass on the top 8 bits of
+// their range with counting inside each bucket, or by LSD radix passes when a
+// bucket is too full -- and every entry reads its rank back through its slot.
+// Leaves with more entries, more than HASH_D distinct keys, a key equal to the
+// empty marker or a key range too wide to pack are LSD-sorted in global
+// memory with their positions alongside.
 constexpr int LG_HT = 12;
 constexpr int HT = 1 << LG_HT;     // table slots, and entries of a leaf on the hash path
 constexpr int HASH_D = HT / 2;     // distinct keys a leaf may hold on the hash path (load <= 1/2)
-constexpr int COUNT_D = T;         // distinct keys ranked by counting; more are radix-sorted
+constexpr int COUNT_D = 32;        // distinct keys ranked by plain counting
 constexpr uint64_t EMPTY = ~0ull;  // marker of a free table slot
 
 struct LsdScratch {
@@ -648,7 +654,7 @@ struct LeafSmem {
     } u;
     uint64_t red_lo[WARPS], red_hi[WARPS];
     uint32_t red_cnt[WARPS];
-    uint32_t nd, bad;
+    uint32_t bad;
 };
 
 __device__ __forceinline__ void leaf_hist(const uint64_t *a, int64_t n, int shift, uint32_t *hist) {
@@ -862,8 +868,9 @@ __device__ void leaf_global(uint64_t *__restrict__ K2, uint64_t *__restrict__ sc
 }
 
 // slot of key x in the table of 2^lg slots, inserting it if absent (linear
-// probing; at most 2^lg probes).  Sets S.bad when x is the empty marker, when
-// the leaf exceeds HASH_D distinct keys, or when no slot was found.
+// probing; at most 2^lg probes).  Sets S.bad when x is the empty marker or
+// when no slot was found.  The distinct keys are counted afterwards, from the
+// table, so that inserts do not meet on one shared counter.
 __device__ __forceinline__ uint32_t hash_insert_slot(uint64_t x, int lg, LeafSmem &S) {
     if (x == EMPTY) {
         S.bad = 1;
@@ -877,16 +884,86 @@ __device__ __forceinline__ uint32_t hash_insert_slot(uint64_t x, int lg, LeafSme
         if (cur == EMPTY) {
             cur = atomicCAS((unsigned long long *)&S.tab[s], (unsigned long long)EMPTY,
                             (unsigned long long)x);
-            if (cur == EMPTY) {
-                if (atomicAdd(&S.nd, 1u) >= (uint32_t)HASH_D) S.bad = 1;
-                return s;
-            }
+            if (cur == EMPTY) return s;
         }
         if (cur == x) return s;
         s = (s + 1) & mask;
     }
     S.bad = 1;
     return 0;
+}
+
+constexpr int MSD_MAX = 64;  // largest bucket the one-pass ordering ranks by counting
+
+// Orders the d packed distinct keys in S.tab[0..d) by one counting pass on the
+// top 8 bits of their range (rb bits above the LG_HT slot bits) into
+// S.tab[HASH_D..), then ranks every key inside its bucket by counting; writes
+// each slot's rank to S.u.sl and the keys to tmpU[ls + rank].  Returns false,
+// having written nothing but its scratch, when a bucket holds more than
+// MSD_MAX keys (the caller then radix-sorts).  Every thread of the block calls
+// it; it ends with a barrier when it succeeds.
+__device__ bool order_by_top_bits(int d, int rb, uint64_t r_lo, int64_t ls,
+                                  uint64_t *__restrict__ tmpU, LeafSmem &S) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t *a = S.tab, *b = S.tab + HASH_D;
+    uint32_t *cnt = S.u.L.hist, *start = S.u.L.run, *fill = S.u.L.ttot;
+    const int sh = LG_HT + (rb > 8 ? rb - 8 : 0);
+    for (int i = threadIdx.x; i < 256; i += T) {
+        cnt[i] = 0;
+        fill[i] = 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += T) atomicAdd(&cnt[(a[i] >> sh) & 255], 1u);
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t c[8], sum = 0, mx = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            c[q] = cnt[lane * 8 + q];
+            sum += c[q];
+            mx = c[q] > mx ? c[q] : mx;
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+            const uint32_t z = __shfl_xor_sync(FULL, mx, o);
+            mx = z > mx ? z : mx;
+        }
+        uint32_t ex = inc - sum;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            start[lane * 8 + q] = ex;
+            ex += c[q];
+        }
+        if (lane == 0) S.u.L.flag = mx;
+    }
+    __syncthreads();
+    if (S.u.L.flag > (uint32_t)MSD_MAX) return false;
+    for (int i = threadIdx.x; i < d; i += T) {
+        const uint64_t m = a[i];
+        const uint32_t g = (uint32_t)(m >> sh) & 255u;
+        b[start[g] + atomicAdd(&fill[g], 1u)] = m;
+    }
+    __syncthreads();
+    uint32_t *R = reinterpret_cast<uint32_t *>(a);  // ranks, over the consumed input
+    for (int j = threadIdx.x; j < d; j += T) {
+        const uint64_t m = b[j];
+        const uint32_t g = (uint32_t)(m >> sh) & 255u;
+        const int s0 = (int)start[g], s1 = s0 + (int)cnt[g];
+        uint32_t r = (uint32_t)s0;
+        for (int k = s0; k < s1; k++) r += b[k] < m;
+        R[j] = r;
+    }
+    __syncthreads();  // the scratch read above shares memory with sl
+    for (int j = threadIdx.x; j < d; j += T) {
+        const uint64_t m = b[j];
+        const uint32_t r = R[j];
+        S.u.sl[m & (HT - 1)] = (uint16_t)r;
+        tmpU[ls + r] = (m >> LG_HT) + r_lo;
+    }
+    return true;
 }
 
 constexpr int HPT = HT / T;  // table slots per thread in the compaction
@@ -917,7 +994,6 @@ __global__ void __launch_bounds__(T, 4)
         const int TS = 1 << lg;
         for (int s = threadIdx.x; s < TS; s += T) S.tab[s] = EMPTY;
         if (threadIdx.x == 0) {
-            S.nd = 0;
             S.bad = 0;
         }
         __syncthreads();
@@ -940,7 +1016,6 @@ __global__ void __launch_bounds__(T, 4)
             leaf_global(K2, scratch, pay, N, ls, n, U2, tmpU, ucnt + leaf, S);
             continue;
         }
-        const int d = (int)S.nd;
         // 2. compact the distinct keys (read all slots first: the packed keys
         //    overwrite the front of the table)
         uint64_t v[HPT];
@@ -966,7 +1041,9 @@ __global__ void __launch_bounds__(T, 4)
         uint64_t r_lo, r_hi;
         block_min_max(lo, hi, S, r_lo, r_hi);  // its barrier also publishes red_cnt
         const int rb = r_hi == r_lo ? 0 : 64 - __clzll((long long)(r_hi - r_lo));
-        if (rb + LG_HT > 64) {
+        int d = 0;
+        for (int w = 0; w < WARPS; w++) d += (int)S.red_cnt[w];
+        if (rb + LG_HT > 64 || d > HASH_D) {
             __syncthreads();  // every thread has read the reductions
             leaf_global(K2, scratch, pay, N, ls, n, U2, tmpU, ucnt + leaf, S);
             continue;
@@ -1014,7 +1091,7 @@ __global__ void __launch_bounds__(T, 4)
                 S.u.sl[m & (HT - 1)] = (uint16_t)r;
                 tmpU[ls + r] = (m >> LG_HT) + r_lo;
             }
-        } else {
+        } else if (!order_by_top_bits(d, rb, r_lo, ls, tmpU, S)) {
             uint32_t *np = nullptr, *nq = nullptr;
             const uint64_t *a =
                 leaf_sort_bits<false>(S.tab, S.tab + HASH_D, np, nq, d, LG_HT, LG_HT + rb, S.u.L);
@@ -1062,7 +1139,7 @@ __global__ void __launch_bounds__(T)
 
 __global__ void __launch_bounds__(T)
     unscatter2(const int64_t *__restrict__ base1, const uint32_t *__restrict__ H1, int G, int B1,
-               const uint8_t *__restrict__ bid2, uint32_t *__restrict__ dest2_u1,
+               const Bid2 *__restrict__ bid2, uint32_t *__restrict__ dest2_u1,
                const uint32_t *__restrict__ U2, const int64_t *__restrict__ ubase) {
     const int b1 = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1166,7 +1243,7 @@ cusci_status run(const Plan &p, const uint64_t *keys, unsigned char *ws, uint64_
     uint16_t *bid1 = (uint16_t *)(ws + p.o_bid1);
     uint64_t *K1 = (uint64_t *)(ws + p.o_K1);
     uint32_t *dest1 = (uint32_t *)(ws + p.o_dest1);
-    uint8_t *bid2 = (uint8_t *)(ws + p.o_bid2);
+    Bid2 *bid2 = (Bid2 *)(ws + p.o_bid2);
     uint64_t *K2 = (uint64_t *)(ws + p.o_K2);
     uint32_t *dest2 = (uint32_t *)(ws + p.o_dest2);
     uint32_t *U2 = (uint32_t *)(ws + p.o_U2);
