@@ -646,15 +646,16 @@ struct LsdScratch {
 };
 
 struct LeafSmem {
-    uint64_t tab[HT];  // hash table; afterwards the two sort buffers tab and tab + HASH_D
-    uint16_t es[HT];   // table slot of every entry of the leaf
+    uint64_t tab[HT];     // hash table; afterwards the two sort buffers tab and tab + HASH_D
+    uint16_t es[HT];      // table slot of every entry of the leaf
+    uint16_t dl[HASH_D];  // slots of the distinct keys, in order of first insertion
     union {
         LsdScratch L;
         uint16_t sl[HT];  // rank of the key held in every slot (written after ordering)
     } u;
     uint64_t red_lo[WARPS], red_hi[WARPS];
     uint32_t red_cnt[WARPS];
-    uint32_t bad;
+    uint32_t nd, bad;
 };
 
 __device__ __forceinline__ void leaf_hist(const uint64_t *a, int64_t n, int shift, uint32_t *hist) {
@@ -868,10 +869,11 @@ __device__ void leaf_global(uint64_t *__restrict__ K2, uint64_t *__restrict__ sc
 }
 
 // slot of key x in the table of 2^lg slots, inserting it if absent (linear
-// probing; at most 2^lg probes).  Sets S.bad when x is the empty marker or
-// when no slot was found.  The distinct keys are counted afterwards, from the
-// table, so that inserts do not meet on one shared counter.
-__device__ __forceinline__ uint32_t hash_insert_slot(uint64_t x, int lg, LeafSmem &S) {
+// probing; at most 2^lg probes); fresh tells whether this call inserted it.
+// Sets S.bad when x is the empty marker or when no slot was found.
+__device__ __forceinline__ uint32_t hash_insert_slot(uint64_t x, int lg, LeafSmem &S,
+                                                     bool &fresh) {
+    fresh = false;
     if (x == EMPTY) {
         S.bad = 1;
         return 0;
@@ -884,7 +886,10 @@ __device__ __forceinline__ uint32_t hash_insert_slot(uint64_t x, int lg, LeafSme
         if (cur == EMPTY) {
             cur = atomicCAS((unsigned long long *)&S.tab[s], (unsigned long long)EMPTY,
                             (unsigned long long)x);
-            if (cur == EMPTY) return s;
+            if (cur == EMPTY) {
+                fresh = true;
+                return s;
+            }
         }
         if (cur == x) return s;
         s = (s + 1) & mask;
@@ -966,7 +971,13 @@ __device__ bool order_by_top_bits(int d, int rb, uint64_t r_lo, int64_t ls,
     return true;
 }
 
-constexpr int HPT = HT / T;  // table slots per thread in the compaction
+constexpr int DPT = HASH_D / T;  // distinct keys per thread in the compaction
+
+// every slot of the table EMPTY, then a barrier
+__device__ __forceinline__ void clear_table(LeafSmem &S) {
+    for (int s = threadIdx.x; s < HT; s += T) S.tab[s] = EMPTY;
+    __syncthreads();
+}
 constexpr int UI = 4;        // keys in flight per thread in the insertion
 
 __global__ void __launch_bounds__(T, 4)
@@ -977,6 +988,7 @@ __global__ void __launch_bounds__(T, 4)
     extern __shared__ __align__(16) unsigned char sm[];
     LeafSmem &S = *reinterpret_cast<LeafSmem *>(sm);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    clear_table(S);
     for (int64_t leaf = blockIdx.x; leaf < NL; leaf += gridDim.x) {
         const int64_t ls = leaf_start[leaf];
         const int64_t n = leaf_start[leaf + 1] - ls;
@@ -988,16 +1000,17 @@ __global__ void __launch_bounds__(T, 4)
             leaf_global(K2, scratch, pay, N, ls, n, U2, tmpU, ucnt + leaf, S);
             continue;
         }
-        // table of 2^lg >= 2n slots (64 at least, HT at most)
+        // table of 2^lg >= 2n slots (64 at least, HT at most); all HT slots are
+        // EMPTY here (cleared before the first leaf and behind every leaf)
         int lg = (n <= 1 ? 0 : 64 - __clzll((long long)(n - 1))) + 1;
         lg = lg < 6 ? 6 : (lg > LG_HT ? LG_HT : lg);
-        const int TS = 1 << lg;
-        for (int s = threadIdx.x; s < TS; s += T) S.tab[s] = EMPTY;
         if (threadIdx.x == 0) {
             S.bad = 0;
+            S.nd = 0;
         }
         __syncthreads();
-        // 1. insert every entry, remembering its slot
+        // 1. insert every entry, remembering its slot; the slots of new keys are
+        //    appended to S.dl (one shared atomic per warp and round)
         for (int64_t k0 = 0; k0 < n; k0 += T * UI) {
             uint64_t x[UI];
 #pragma unroll
@@ -1008,54 +1021,60 @@ __global__ void __launch_bounds__(T, 4)
 #pragma unroll
             for (int u = 0; u < UI; u++) {
                 const int64_t k = k0 + u * T + threadIdx.x;
-                if (k < n) S.es[k] = (uint16_t)hash_insert_slot(x[u], lg, S);
+                bool fresh = false;
+                uint32_t slot = 0;
+                if (k < n) {
+                    slot = hash_insert_slot(x[u], lg, S, fresh);
+                    S.es[k] = (uint16_t)slot;
+                }
+                const unsigned bal = __ballot_sync(FULL, fresh);
+                if (bal) {
+                    const int lead = __ffs(bal) - 1;
+                    uint32_t base = 0;
+                    if (lane == lead) base = atomicAdd(&S.nd, (uint32_t)__popc(bal));
+                    base = __shfl_sync(FULL, base, lead);
+                    const uint32_t i = base + __popc(bal & ((1u << lane) - 1u));
+                    if (fresh && i < (uint32_t)HASH_D) S.dl[i] = (uint16_t)slot;
+                }
             }
         }
         __syncthreads();
-        if (S.bad) {
+        const int d = (int)S.nd;
+        if (S.bad || d > HASH_D) {
             leaf_global(K2, scratch, pay, N, ls, n, U2, tmpU, ucnt + leaf, S);
+            clear_table(S);
             continue;
         }
-        // 2. compact the distinct keys (read all slots first: the packed keys
-        //    overwrite the front of the table)
-        uint64_t v[HPT];
+        // 2. the distinct keys (all read before the packed keys overwrite the
+        //    table front), their range, and the packed keys in tab[0..d)
+        uint64_t v[DPT];
+        uint32_t sv[DPT];
         uint64_t lo = ~0ull, hi = 0;
-        uint32_t cnt = 0;
 #pragma unroll
-        for (int j = 0; j < HPT; j++) {
-            const int s = j * T + threadIdx.x;
-            v[j] = s < TS ? S.tab[s] : EMPTY;
-            if (v[j] != EMPTY) {
+        for (int j = 0; j < DPT; j++) {
+            const int i = j * T + threadIdx.x;
+            sv[j] = 0;
+            v[j] = 0;
+            if (i < d) {
+                sv[j] = S.dl[i];
+                v[j] = S.tab[sv[j]];
                 lo = v[j] < lo ? v[j] : lo;
                 hi = v[j] > hi ? v[j] : hi;
-                cnt++;
             }
         }
-        uint32_t inc = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) S.red_cnt[wid] = inc;
         uint64_t r_lo, r_hi;
-        block_min_max(lo, hi, S, r_lo, r_hi);  // its barrier also publishes red_cnt
+        block_min_max(lo, hi, S, r_lo, r_hi);
         const int rb = r_hi == r_lo ? 0 : 64 - __clzll((long long)(r_hi - r_lo));
-        int d = 0;
-        for (int w = 0; w < WARPS; w++) d += (int)S.red_cnt[w];
-        if (rb + LG_HT > 64 || d > HASH_D) {
+        if (rb + LG_HT > 64) {
             __syncthreads();  // every thread has read the reductions
             leaf_global(K2, scratch, pay, N, ls, n, U2, tmpU, ucnt + leaf, S);
+            clear_table(S);
             continue;
         }
-        uint32_t pos = inc - cnt;
-        for (int w = 0; w < wid; w++) pos += S.red_cnt[w];
 #pragma unroll
-        for (int j = 0; j < HPT; j++) {
-            if (v[j] != EMPTY) {
-                const uint64_t s = (uint64_t)(j * T + threadIdx.x);
-                S.tab[pos++] = ((v[j] - r_lo) << LG_HT) | s;
-            }
+        for (int j = 0; j < DPT; j++) {
+            const int i = j * T + threadIdx.x;
+            if (i < d) S.tab[i] = ((v[j] - r_lo) << LG_HT) | sv[j];
         }
         // rank counters of the counting path, behind the packed keys (d <= T)
         uint32_t *rank = reinterpret_cast<uint32_t *>(S.tab + HASH_D);
@@ -1103,10 +1122,17 @@ __global__ void __launch_bounds__(T, 4)
             }
         }
         __syncthreads();
-        // 4. the local unique id of every entry
+        // 4. the local unique id of every entry; behind it the table is made
+        //    EMPTY again where this leaf touched it: the occupied slots, the
+        //    packed keys / ranks in [0, d) and the second buffer [HASH_D, +d)
         for (int k = threadIdx.x; k < (int)n; k += T) U2[ls + k] = S.u.sl[S.es[k]];
+        for (int i = threadIdx.x; i < d; i += T) {
+            S.tab[S.dl[i]] = EMPTY;
+            S.tab[i] = EMPTY;
+            S.tab[HASH_D + i] = EMPTY;
+        }
         if (threadIdx.x == 0) ucnt[leaf] = d;
-        __syncthreads();  // before the next leaf resets the table
+        __syncthreads();  // before the next leaf inserts
     }
 }
 
