@@ -230,7 +230,9 @@ static Plan make_plan(int64_t total, int W, int n_bits, int n_ones) {
     if (p.key_bits < 1) p.key_bits = 1;
     p.passes = (p.key_bits + RBITS - 1) / RBITS;
     int64_t tiles = (total + RTILE - 1) / RTILE;
-    int64_t g = (int64_t)sm_count() * 2;
+    // resident blocks per SM of the downsweep (registers bound it: 3 for
+    // two-word keys, 4 for one-word keys)
+    int64_t g = (int64_t)sm_count() * (p.KW == 2 ? 3 : 4);
     if (g > tiles) g = tiles;
     if (g < 1) g = 1;
     int64_t tiles_per = (tiles + g - 1) / g;

@@ -8,8 +8,8 @@ namespace cusci {
 namespace radix {
 
 constexpr int RT = 256;          // threads per CTA
-constexpr int RI = 16;           // keys per thread per tile
-constexpr int RTILE = RT * RI;   // 4096
+constexpr int RI = 8;            // keys per thread per tile
+constexpr int RTILE = RT * RI;   // 2048
 constexpr int RBITS = 8;
 constexpr int RADIX = 1 << RBITS;
 constexpr int RWARPS = RT / 32;
@@ -25,8 +25,10 @@ struct Key {
 template <int KW>
 __device__ __forceinline__ uint32_t digit_of(const Key<KW> &k, int shift) {
     if (KW == 1) return (uint32_t)((k.w[0] >> shift) & (RADIX - 1));
+    // KW == 2; the word is chosen by a select, not an index, so that keys held
+    // in registers are not moved to local memory
     const int word = shift >> 6, sh = shift & 63;
-    uint64_t lo = k.w[word] >> sh;
+    uint64_t lo = (word == 0 ? k.w[0] : k.w[KW - 1]) >> sh;
     if (sh > 64 - RBITS && word + 1 < KW) lo |= k.w[KW - 1] << (64 - sh);
     return (uint32_t)(lo & (RADIX - 1));
 }
