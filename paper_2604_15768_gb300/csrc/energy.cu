@@ -7,7 +7,8 @@
 // open-addressing hash table of S built in the caller's workspace (S is 1.6 MB
 // of keys for 200k determinants, so the table stays in L2).  An exact
 // prefilter skips the probe for targets farther from S[0] -- per spin or in
-// total -- than every member of S.
+// total -- than every member of S, and a one-bit-per-hash filter of S (16 bits
+// per member, L2-resident) skips it for almost every other non-member.
 // Reductions are deterministic: per-row warp shuffles in a fixed pattern, then
 // one block that sums rows in a fixed order (Neumaier-compensated per thread)
 // followed by a fixed tree -- no floating-point atomics.
@@ -37,7 +38,18 @@ struct Table {
     int shift;        // 64 - log2(cap)
     const uint64_t *ref;       // S[0]
     const uint32_t *maxdist;   // [3]: largest alpha, beta and total distance of S from S[0]
+    uint32_t *bloom;           // one bit per 2^-bshift of a second hash: set for every member
+    int bshift;                // 64 - log2(bloom bits)
 };
+
+// the filter bit of a determinant: a second multiplicative hash, independent
+// of the table slot; a clear bit proves the determinant is not in S
+template <int W>
+__device__ __forceinline__ uint64_t bloom_bit(const uint64_t *d, int bshift) {
+    uint64_t x = d[0];
+    if (W == 2) x ^= d[W - 1] * 0x9fb21c651e98df25ull;
+    return (x * 0xd6e8feb86659fd93ull) >> bshift;
+}
 
 // occupation differences of t from the reference, per spin
 template <int W>
@@ -79,6 +91,8 @@ __global__ void insert_S(Table tb, const uint64_t *__restrict__ S, int64_t nS,
         atomicMax(maxdist, da);
         atomicMax(maxdist + 1, db);
         atomicMax(maxdist + 2, da + db);
+        const uint64_t bb = bloom_bit<W>(d, tb.bshift);
+        atomicOr(tb.bloom + (bb >> 5), 1u << (bb & 31));
         uint64_t h = hash_det<W>(d, tb.shift);
         for (uint64_t probe = 0; probe <= tb.mask; probe++) {
             unsigned long long old =
@@ -101,6 +115,9 @@ __device__ __forceinline__ int64_t lookup(const Table &tb, const uint64_t (&t)[W
     spin_dist<W>(t, tb.ref, da, db);
     if (da > __ldg(tb.maxdist) || db > __ldg(tb.maxdist + 1) || da + db > __ldg(tb.maxdist + 2))
         return -1;
+    // most targets are not in S: one filter word (L1/L2) instead of a probe sequence
+    const uint64_t bb = bloom_bit<W>(t, tb.bshift);
+    if (!((__ldg(tb.bloom + (bb >> 5)) >> (bb & 31)) & 1u)) return -1;
     uint64_t h = hash_det<W>(t, tb.shift);
     for (uint64_t probe = 0; probe <= tb.mask; probe++) {
         const int64_t v = __ldg(tb.vals + h);
@@ -224,8 +241,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct EPlan {
     uint64_t cap;
-    int log2cap;
-    size_t off_keys, off_vals, off_hp, off_md, bytes;
+    int log2cap, log2bloom;
+    size_t off_keys, off_vals, off_hp, off_md, off_bloom, bytes;
 };
 
 EPlan eplan(int64_t nS, int W) {
@@ -238,6 +255,11 @@ EPlan eplan(int64_t nS, int W) {
     p.off_vals = off; off = align256(off + p.cap * 8);
     p.off_hp = off; off = align256(off + (size_t)(nS > 0 ? nS : 1) * 8);
     p.off_md = off; off = align256(off + 16);
+    // filter: a power of two of at least 16 bits per member (false positives
+    // about 6%), at least 2^12 bits
+    p.log2bloom = 12;
+    while ((1ull << p.log2bloom) < (uint64_t)(nS > 0 ? nS : 1) * 16) p.log2bloom++;
+    p.off_bloom = off; off = align256(off + ((size_t)1 << p.log2bloom) / 8);
     p.bytes = off;
     return p;
 }
@@ -252,8 +274,9 @@ cusci_status compute_hpsi(const cusci_system *sys, const uint64_t *d_S, int64_t 
     unsigned char *ws = (unsigned char *)d_ws;
     uint32_t *md = (uint32_t *)(ws + p.off_md);
     Table tb{(uint64_t *)(ws + p.off_keys), (int64_t *)(ws + p.off_vals), p.cap - 1,
-             64 - p.log2cap, d_S, md};
+             64 - p.log2cap, d_S, md, (uint32_t *)(ws + p.off_bloom), 64 - p.log2bloom};
     cudaError_t e = cudaMemsetAsync(tb.vals, 0, p.cap * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tb.bloom, 0, ((size_t)1 << p.log2bloom) / 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(md, 0, 16, st);
     if (e != cudaSuccess) return cuda_fail(e, "energy: table clear");
     const uint64_t *mask = NULL;
