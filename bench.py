@@ -842,9 +842,17 @@ def main(argv=None):
     ap.add_argument("--batch-wave-entries", type=float, default=1.2e9)
     ap.add_argument("--profile-sources", type=int, default=None,
                     help="profiling driver: count/scan/fill/dedup of this many sources only")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="profiling driver: the batched leg alone (at --batch-scale)")
     args = ap.parse_args(argv)
     if args.profile_sources:
         return run_profile(args)
+    if args.profile_batched:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"profile": "batched", "batched": run_batched(args, torch.device("cuda:0"))}),
+              flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
