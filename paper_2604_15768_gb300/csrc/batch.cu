@@ -37,6 +37,7 @@ struct cusci_batch {
     // count (device int2[n_sys]) and the base of its rank range in the joint
     // key space (device uint64[n_sys + 1]; base[n_sys] = size of that space)
     int2 *d_sysinfo;
+    int max_bits = 0, max_ones = 0;  // over the systems: M and n_alpha + n_beta
     uint64_t *d_base;
     int64_t *d_src_begin;            // device copy of src_begin (first dedup call)
     bool d_src_begin_ready;
@@ -255,13 +256,46 @@ __global__ void bd_ebeg(const int64_t *__restrict__ offsets, const int64_t *__re
     if (k <= n_sys) ebeg[k] = offsets[src_begin[k]];
 }
 
+// Shared-memory copies for the rank kernels: C(m, c) for m < bm, c < bk at
+// [m * bk + c], and the n_sys + 1 system boundaries of the index being
+// searched.  Staged when they fit in BD_SMEM bytes (else read from global).
+constexpr size_t BD_SMEM = 48 * 1024;
+
+size_t bd_smem_bytes(int bm, int bk, int n_sys) {
+    const size_t b = (size_t)bm * bk * 8 + (size_t)(n_sys + 1) * 8;
+    return b <= BD_SMEM ? b : 0;
+}
+
+struct BdTables {
+    const uint64_t *binom;  // [m * stride + c]
+    int stride;
+    const int64_t *bounds;  // n_sys + 1 system boundaries
+};
+
+__device__ BdTables bd_stage(bool staged, int bm, int bk, int n_sys,
+                             const int64_t *__restrict__ bounds) {
+    extern __shared__ __align__(16) unsigned char bdsm[];
+    if (!staged) return BdTables{g_bbinom, 65, bounds};
+    uint64_t *sb = reinterpret_cast<uint64_t *>(bdsm);
+    int64_t *sbd = reinterpret_cast<int64_t *>(bdsm + (size_t)bm * bk * 8);
+    for (int i = threadIdx.x; i < bm * bk; i += blockDim.x) {
+        const int m = i / bk, c = i - m * bk;
+        sb[i] = g_bbinom[m * 65 + c];
+    }
+    for (int i = threadIdx.x; i <= n_sys; i += blockDim.x) sbd[i] = bounds[i];
+    __syncthreads();
+    return BdTables{sb, bk, sbd};
+}
+
 __global__ void bd_keys(const uint64_t *__restrict__ tgt, int64_t total,
                         const int64_t *__restrict__ ebeg, int n_sys,
                         const int2 *__restrict__ info, const uint64_t *__restrict__ base,
-                        uint64_t *__restrict__ keys, int32_t *__restrict__ status) {
+                        uint64_t *__restrict__ keys, int32_t *__restrict__ status, int staged,
+                        int bm, int bk) {
+    const BdTables tb = bd_stage(staged != 0, bm, bk, n_sys, ebeg);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int k = seg_of(ebeg, n_sys + 1, e);
+        const int k = seg_of(tb.bounds, n_sys + 1, e);
         const int2 in = info[k];
         uint64_t r = 0;
         int c = 0;
@@ -275,7 +309,7 @@ __global__ void bd_keys(const uint64_t *__restrict__ tgt, int64_t total,
             for (x &= keep; x; x &= x - 1) {
                 const int pos = 64 * w + __ffsll((long long)x) - 1;
                 c++;
-                if (c <= 64) r += g_bbinom[pos * 65 + c];
+                if (c < tb.stride) r += tb.binom[pos * tb.stride + c];
             }
         }
         if ((bad || c != in.y) && status) *status = CUSCI_ERR_INVALID;
@@ -311,24 +345,27 @@ __global__ void bd_bounds(const uint64_t *__restrict__ uniq, const int64_t *__re
 __global__ void bd_unrank(const uint64_t *__restrict__ uniq, const int64_t *__restrict__ d_nu,
                           const int64_t *__restrict__ ub, const int64_t *__restrict__ ebeg,
                           int n_sys, const int2 *__restrict__ info,
-                          const uint64_t *__restrict__ base, uint64_t *__restrict__ out) {
+                          const uint64_t *__restrict__ base, uint64_t *__restrict__ out,
+                          int staged, int bm, int bk) {
+    const BdTables tb = bd_stage(staged != 0, bm, bk, n_sys, ub);
     const int64_t nu = *d_nu;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nu;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const int k = seg_of(ub, n_sys + 1, j);
+        const int k = seg_of(tb.bounds, n_sys + 1, j);
         const int2 in = info[k];
         uint64_t v = uniq[j] - base[k];
-        uint64_t d[2] = {0ull, 0ull};
+        uint64_t d0 = 0ull, d1 = 0ull;  // two words held in registers
         int p = in.x - 1;
         for (int c = in.y; c >= 1; c--) {
-            while (p >= c && g_bbinom[p * 65 + c] > v) p--;
-            if (p >= c) v -= g_bbinom[p * 65 + c];
-            if (p >= 0) d[p >> 6] |= 1ull << (p & 63);
+            while (p >= c && tb.binom[p * tb.stride + c] > v) p--;
+            if (p >= c) v -= tb.binom[p * tb.stride + c];
+            if (p >= 64) d1 |= 1ull << (p - 64);
+            else if (p >= 0) d0 |= 1ull << p;
             p--;
         }
-        const int64_t at = ebeg[k] + (j - ub[k]);
-        out[2 * at] = d[0];
-        out[2 * at + 1] = d[1];
+        const int64_t at = ebeg[k] + (j - tb.bounds[k]);
+        out[2 * at] = d0;
+        out[2 * at + 1] = d1;
     }
 }
 
@@ -388,6 +425,8 @@ extern "C" cusci_status cusci_batch_create(const cusci_system *const *systems, i
     bool fits = true;
     for (int k = 0; k < n_systems; k++) {
         info[k] = make_int2(systems[k]->M, systems[k]->n_alpha + systems[k]->n_beta);
+        if (info[k].x > b->max_bits) b->max_bits = info[k].x;
+        if (info[k].y > b->max_ones) b->max_ones = info[k].y;
         const unsigned __int128 c = binom_u128(info[k].x, info[k].y);
         const unsigned __int128 nb = (unsigned __int128)base[k] + c;
         if (c > (unsigned __int128)~0ull || nb > (unsigned __int128)~0ull) fits = false;
@@ -524,14 +563,18 @@ extern "C" cusci_status cusci_batch_dedup(cusci_batch *b, const int64_t *d_offse
     int blocks = (int)((total + 255) / 256);
     if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     bd_ebeg<<<1, 128 * ((ns + 128) / 128), 0, st>>>(d_offsets, b->d_src_begin, ns, ebeg);
-    bd_keys<<<blocks, 256, 0, st>>>(d_targets, total, ebeg, ns, b->d_sysinfo, b->d_base, keys,
-                                    d_status);
+    // binomial rows up to the largest M and electron count of the batch
+    const int bm = b->max_bits, bk = b->max_ones + 1;
+    const size_t bsm = bd_smem_bytes(bm, bk, ns);
+    bd_keys<<<blocks, 256, bsm, st>>>(d_targets, total, ebeg, ns, b->d_sysinfo, b->d_base, keys,
+                                      d_status, bsm > 0 ? 1 : 0, bm, bk);
     CUSCI_LAUNCHED(2, "batched dedup keys");
     rc = cusci_dedup(keys, total, 1, b->key_bits, -1, inner, inner_bytes, uniq, d_inverse, 4, d_nu,
                      NULL, d_status, stream);
     if (rc != CUSCI_OK) return rc;
     bd_bounds<<<1, 128 * ((ns + 128) / 128), 0, st>>>(uniq, d_nu, b->d_base, ns, ub, d_n_unique);
-    bd_unrank<<<blocks, 256, 0, st>>>(uniq, d_nu, ub, ebeg, ns, b->d_sysinfo, b->d_base, d_unique);
+    bd_unrank<<<blocks, 256, bsm, st>>>(uniq, d_nu, ub, ebeg, ns, b->d_sysinfo, b->d_base,
+                                        d_unique, bsm > 0 ? 1 : 0, bm, bk);
     bd_localize<<<blocks, 256, 0, st>>>(d_inverse, total, ebeg, ns, ub);
     CUSCI_LAUNCHED(3, "batched dedup split");
     return CUSCI_OK;
