@@ -147,7 +147,7 @@ __device__ __forceinline__ int lanes_below(uint32_t ballot, int lane) {
 
 // ---------------------------------------------------------------- count pass
 template <int W>
-__device__ int64_t count_source(const SysView &v, const Src<W> &s, double eps, int lane) {
+__device__ __forceinline__ int64_t count_source(const SysView &v, const Src<W> &s, double eps, int lane) {
     const int n = v.norb;
     const int nchunk = (n + 31) >> 5;
     uint32_t singles = 0;
