@@ -898,7 +898,7 @@ __device__ __forceinline__ uint32_t hash_insert_slot(uint64_t x, int lg, LeafSme
     return 0;
 }
 
-constexpr int MSD_MAX = 64;  // largest bucket the one-pass ordering ranks by counting
+constexpr int MSD_MAX = 128; // largest bucket the one-pass ordering ranks by counting
 
 // Orders the d packed distinct keys in S.tab[0..d) by one counting pass on the
 // top 8 bits of their range (rb bits above the LG_HT slot bits) into
