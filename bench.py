@@ -52,7 +52,7 @@ TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 117.35, "cusci_gen_coupled (fill_kernel)":
 # the same capture per phase of the dedup call (the phase names of
 # cusci_dedup_phase_name; scans and tiny launches folded into their phase)
 DEDUP_KERNEL_B_PER_ENTRY = {"sample+splitters": 0.91, "hist1": 9.95, "scatter1": 25.12,
-                            "level2": 32.76, "leaf_dedup": 14.87, "compact_unique": 5.00,
+                            "level2": 32.76, "leaf_dedup": 14.88, "compact_unique": 5.00,
                             "unscatter2": 16.81, "unscatter1": 11.91}
 UNIT = "entries/s"
 
