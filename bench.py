@@ -727,9 +727,29 @@ def run_stream(args, dev):
                                    status=rstatus)
         rts.append(time.perf_counter() - t0)
     rt = min(rts)
+    # the hashed form: a table of the distinct set built once, then probed by
+    # every streamed batch (what a repeated Stage-3 query of one set costs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rtab = cusci.reverse_table(uniq, status=rstatus)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    h_inv2 = torch.empty_like(h_inv).pin_memory()
+    tts = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cusci.reverse_index_stream(uniq, hd[:total_e], batch=batch, host_out=h_inv2,
+                                   status=rstatus, table=rtab)
+        tts.append(time.perf_counter() - t0)
+    tt = min(tts)
+    del rtab
     rev = {"entries_per_s": total_e / rt, "ms": rt * 1e3,
            "h2d_bytes": total_e * 8 * sysd.W, "d2h_bytes": total_e * 4,
            "transfer_gbs": total_e * (8 * sysd.W + 4) / rt / 1e9,
+           "hashed": {"table_build_ms": t_build * 1e3, "ms": tt * 1e3,
+                      "entries_per_s": total_e / tt,
+                      "same_ids": bool(torch.equal(h_inv, h_inv2))},
            "status": int(rstatus.item())}
     hbm_peak, _ = _peaks()
     # W = 2: 16 + 8 written per entry, 16 read + 4 inverse-equivalent + 16 per distinct key

@@ -301,6 +301,24 @@ cusci_status cusci_partition_split(const uint64_t *d_unique, int W, const int64_
 cusci_status cusci_reverse_index(const uint64_t *d_unique, int64_t n_unique, int W,
                                  const uint64_t *d_keys, int64_t n, void *d_inverse,
                                  int index_bytes, int32_t *d_status, void *stream);
+/* The same reverse index through a hash table of the distinct set, built once
+ * and then probed by every batch (about one random access per key instead of
+ * a search).  cusci_reverse_table_bytes: bytes of the table for n_unique keys
+ * of W words (a power of two of at least 1.5 n_unique slots; key words, then
+ * an int64 position per slot).  cusci_reverse_table_build fills the caller's
+ * d_table (device, 16-byte aligned, >= that many bytes) from d_unique (device
+ * [n_unique][W], distinct keys; asynchronous; d_status set to
+ * CUSCI_ERR_OVERFLOW if a key found no slot, which the sizing rules out).
+ * cusci_reverse_index_table: d_inverse[k] = position of key k in d_unique,
+ * or -1 with d_status (nullable) set to CUSCI_ERR_INVALID when absent; same
+ * n_unique and W as the build; index_bytes 4 or 8.  Asynchronous. */
+cusci_status cusci_reverse_table_bytes(int64_t n_unique, int W, size_t *bytes);
+cusci_status cusci_reverse_table_build(const uint64_t *d_unique, int64_t n_unique, int W,
+                                       void *d_table, size_t table_bytes, int32_t *d_status,
+                                       void *stream);
+cusci_status cusci_reverse_index_table(const void *d_table, int64_t n_unique, int W,
+                                       const uint64_t *d_keys, int64_t n, void *d_inverse,
+                                       int index_bytes, int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------ top-K selection
  * Streaming two-level top-K (Stage 2 of Sec. 3, the running best set of

@@ -77,6 +77,9 @@ _PROTOS = {
     "cusci_local_energy_bwd": (_I, [_P, _I64, _P, _P, _I, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ,
                                     _P]),
     "cusci_partition_plan": (_I, [_P, _I, _P, _I, _I, _P, _P, _P]),
+    "cusci_reverse_table_bytes": (_I, [_I64, _I, ctypes.POINTER(_SZ)]),
+    "cusci_reverse_table_build": (_I, [_P, _I64, _I, _P, _SZ, _P, _P]),
+    "cusci_reverse_index_table": (_I, [_P, _I64, _I, _P, _I64, _P, _I, _P, _P]),
     "cusci_rank_join": (_I, [_P, _I, _I64, _P, _I, _I, _P, _P, _P]),
     "cusci_rank_runs": (_I, [_P, _I, _P, _I64, _I, _I, _P, _P, _P]),
     "cusci_partition_exchange": (_I, [_P, _I, _I, _P, _P, _P, _P]),
@@ -488,15 +491,48 @@ def reverse_index(unique: torch.Tensor, keys: torch.Tensor, index_bytes: int = 4
     return out
 
 
+def reverse_table(unique: torch.Tensor, status=None, stream=None) -> torch.Tensor:
+    """Hash table of the distinct set for cusci_reverse_index_table (device bytes)."""
+    n_u, W = unique.shape
+    nb = ctypes.c_size_t()
+    _check(load().cusci_reverse_table_bytes(int(n_u), W, ctypes.byref(nb)),
+           "cusci_reverse_table_bytes")
+    table = torch.empty(nb.value, dtype=torch.uint8, device=unique.device)
+    _check(load().cusci_reverse_table_build(_ptr(unique), int(n_u), W, _ptr(table), table.numel(),
+                                            _ptr(status), _stream(stream)),
+           "cusci_reverse_table_build")
+    return table
+
+
+def reverse_index_table(table: torch.Tensor, n_unique: int, W: int, keys: torch.Tensor,
+                        index_bytes: int = 4, out=None, status=None, stream=None):
+    """Position of every key in the distinct set, through its hash table."""
+    if out is None:
+        out = torch.empty(keys.shape[0], dtype=torch.int32 if index_bytes == 4 else torch.int64,
+                          device=keys.device)
+    _check(load().cusci_reverse_index_table(_ptr(table), int(n_unique), W, _ptr(keys),
+                                            keys.shape[0], _ptr(out), index_bytes, _ptr(status),
+                                            _stream(stream)), "cusci_reverse_index_table")
+    return out
+
+
 def reverse_index_stream(unique: torch.Tensor, host_keys: torch.Tensor, batch: int,
-                         host_out: torch.Tensor | None = None, status=None):
+                         host_out: torch.Tensor | None = None, status=None, table=False):
     """Reverse index of a host-resident (pinned) key array against the device
-    distinct set, in batches: copy in, search and copy out on two alternating
-    streams so transfers overlap the searches.  Returns the pinned host ids."""
+    distinct set, in batches: copy in, look up and copy out on two alternating
+    streams so transfers overlap the lookups.  ``table``: a hash table from
+    reverse_table (probed by every batch; worth building when the distinct set
+    is queried more than once), True to build one here, or False to search the
+    sorted set for every key.  Returns the pinned host ids."""
     n, W = host_keys.shape
+    n_u = unique.shape[0]
     dev = unique.device
     if host_out is None:
         host_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    if isinstance(table, torch.Tensor):
+        tb = table
+    else:
+        tb = reverse_table(unique, status=status) if table and n > 0 else None
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     kbuf = [torch.empty((batch, W), dtype=torch.int64, device=dev) for _ in range(2)]
     ibuf = [torch.empty(batch, dtype=torch.int32, device=dev) for _ in range(2)]
@@ -507,7 +543,10 @@ def reverse_index_stream(unique: torch.Tensor, host_keys: torch.Tensor, batch: i
         with torch.cuda.stream(s):
             kb, ib = kbuf[t & 1][:b - a], ibuf[t & 1][:b - a]
             kb.copy_(host_keys[a:b], non_blocking=True)
-            reverse_index(unique, kb, 4, out=ib, status=status, stream=s)
+            if tb is not None:
+                reverse_index_table(tb, n_u, W, kb, 4, out=ib, status=status, stream=s)
+            else:
+                reverse_index(unique, kb, 4, out=ib, status=status, stream=s)
             host_out[a:b].copy_(ib, non_blocking=True)
     for s in streams:
         s.synchronize()
