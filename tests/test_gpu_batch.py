@@ -1,6 +1,8 @@
 """Many independent systems in one persistent launch: per system, the coupled
 lists and the de-duplication equal the oracle's (and the single-system path),
 also when the whole sequence is replayed from a CUDA graph."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -99,3 +101,18 @@ def test_batch_replay_unaffected_by_other_eps_on_its_systems(batch):
     b.replay()
     torch.cuda.synchronize()
     check_all(systems, b)
+
+
+def test_batch_edge_cases_single_system_one_source_and_twins():
+    """A batch of one system; a system with a single source; two identical
+    systems side by side (their joint keys must stay apart, so each keeps its
+    own distinct set and ids)."""
+    base = synth.batched_systems(6, scale=0.02)
+    one_src = dataclasses.replace(base[1], dets=base[1].dets[:1])
+    for systems in ([base[0]], [one_src, base[2]], [base[3], base[3], base[4]]):
+        b = cusci.Batch(systems, [s.dets for s in systems], 1e-8, chunk=2)
+        b.plan()
+        b.run()
+        torch.cuda.synchronize()
+        check_all(systems, b)
+        b.close()
