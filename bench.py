@@ -399,6 +399,12 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, s, sysd, dev) if args.e2e else None
+    if e2e is not None and ws > 1:
+        # whole job: every rank's entries over the slowest rank's step
+        e_ms, e_entries = aggregate_over_ranks(e2e["ms_per_step"], total, device=dev)
+        e2e.update({"value": e_entries / (e_ms * 1e-3), "ms_per_step": e_ms,
+                    "h2d_bytes_per_step": e2e["h2d_bytes_per_step"] * ws,
+                    "d2h_bytes_per_step": e2e["d2h_bytes_per_step"] * ws})
     torch.cuda.empty_cache()
 
     # energy forward + adjoint on the 200k selected set
