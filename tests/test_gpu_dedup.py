@@ -230,3 +230,22 @@ def test_kernel_timing_records_every_phase():
     assert list(ms) == ["sample+splitters", "hist1", "scatter1", "level2", "leaf_dedup",
                         "compact_unique", "unscatter2", "unscatter1"]
     assert all(v > 0 for v in ms.values())
+
+
+@pytest.mark.parametrize("n", [(1 << 22) - 1, 1 << 22])
+def test_path_threshold_both_sides(n):
+    """Just below and at the size where the sample-sort path takes over from
+    the LSD path: identical results, equal to the oracle's."""
+    rng = np.random.default_rng(40 + n % 7)
+    base = rng.integers(0, 1 << 44, size=n // 3).astype(np.uint64)
+    keys = base[rng.integers(0, base.size, size=n)].reshape(-1, 1)
+    compare(keys, 44, -1)
+
+
+def test_sample_sort_single_distinct_key():
+    """Every key equal at sample-sort size: all splitters coincide, one leaf
+    holds everything (global-memory path), one distinct key, inverse all zero."""
+    keys = np.full((4_300_000, 1), 987654321, dtype=np.uint64)
+    u, inv, nu = gpu_dedup(keys, 40, -1)
+    assert nu == 1 and u.shape[0] >= 1 and int(u[0, 0]) == 987654321
+    assert (inv == 0).all()
