@@ -73,3 +73,26 @@ def test_local_energy_equals_variational_on_closed_space():
     sysd = cusci.System.of(s)
     Ev, n2v, hp = cusci.energy_fwd(sysd, to_dev(s.dets), psi, s.eps)
     assert abs(E.item() - Ev.item()) <= 1e-10
+
+
+@pytest.mark.parametrize("name,n,scale", [("large", 20, 1.0), ("mid", 200, 50.0)])
+def test_local_energy_two_words_and_large_mixed_sign_amplitudes(name, n, scale):
+    """Two-word configurations, and amplitudes of both signs and large size, so
+    that the fixed-point adjoint accumulates terms with integer parts well
+    away from 0 and -1 (carries into and borrows from the high word)."""
+    s = synth.config_system(name)
+    off, oh, inv, nu = pipeline(s, n)
+    rng = np.random.default_rng(9)
+    psi = rng.standard_normal(nu) * scale + (1.0 if scale == 1.0 else 0.0)
+    dpsi = torch.from_numpy(psi).cuda()
+    E, n2, y = cusci.local_energy_fwd(off, oh, inv, dpsi)
+    grad = cusci.local_energy_bwd(off, oh, inv, dpsi, E, n2, y=y)
+    grad2 = cusci.local_energy_bwd(off, oh, inv, dpsi, E, n2, y=y)
+    torch.cuda.synchronize()
+    oE, on2, oy, og = O.local_energy(off.cpu().numpy(), oh.cpu().numpy(),
+                                     inv.cpu().numpy().astype(np.int64), psi)
+    assert abs(E.item() - oE) <= 1e-10 * max(1.0, abs(oE))
+    assert np.abs(y.cpu().numpy() - oy).max() <= 1e-10 * max(1.0, np.abs(oy).max())
+    g = grad.cpu().numpy()
+    assert np.abs(g - og).max() <= 1e-10 * max(1.0, np.abs(og).max())
+    assert np.array_equal(g, grad2.cpu().numpy())
