@@ -344,7 +344,10 @@ cusci_status cusci_topk_update(const double *d_scores, const int64_t *d_ids, int
  * offload of the original coupled set to host memory).
  * h_dets: host [n][W] sources.  d_pool: device memory of pool_bytes, 256-byte
  * aligned, at least cusci_stream_pool_bytes(); the library uses nothing else
- * on the device.  batch_entries: capacity of one mini-batch (two are in flight:
+ * on the device.  The pool holds the per-source arrays, a hash set of the
+ * distinct keys (at most 3/4 full at unique_capacity) and the two batch
+ * buffers; the final sort of the distinct keys then reuses the hash set's
+ * memory.  batch_entries: capacity of one mini-batch (two are in flight:
  * one filled while the other is copied out); every single source's list must
  * fit one batch.  h_offsets: host int64[n+1], receives the CSR offsets of the
  * whole coupled set.  h_out_dets / h_out_h: host sinks (pinned for overlap)
