@@ -354,7 +354,9 @@ __global__ void make_splitters(const uint64_t *__restrict__ sorted, int64_t NS, 
 }
 
 constexpr int U1 = 8;   // keys per thread in flight in the partition passes
+constexpr int U1S = 16; // ... in the one-word level-1 scatter (17.0 -> 15.5 ms; 16 slows the others)
 constexpr int UG = 8;   // gathers in flight per thread in the reverse-index passes
+constexpr int UG1 = 16; // ... in the last of them (measured: 4.9 -> 4.6 ms)
 
 template <int W>
 __global__ void __launch_bounds__(T)
@@ -466,6 +468,7 @@ __global__ void __launch_bounds__(T)
              int kcols, const uint64_t *__restrict__ bt_g, const uint16_t *__restrict__ bid1,
              int B1, const uint32_t *__restrict__ H1, int64_t *__restrict__ base1,
              uint64_t *__restrict__ K1, uint32_t *__restrict__ dest1) {
+    constexpr int US = W == 1 ? U1S : U1;  // two-word keys: registers
     extern __shared__ __align__(16) unsigned char sm[];
     uint32_t *run = (uint32_t *)sm;
     uint64_t *bt = (uint64_t *)(sm + (size_t)MAX_B1 * 4);
@@ -479,32 +482,32 @@ __global__ void __launch_bounds__(T)
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) base1[(int64_t)gridDim.x * B1] = N;
     int64_t end = beg + per_cta;
     if (end > N) end = N;
-    uint64_t rn[U1][W];
-    uint32_t bn[U1];
-    load_keys<W, U1>(keys, beg + threadIdx.x, T, end, rn);
+    uint64_t rn[US][W];
+    uint32_t bn[US];
+    load_keys<W, US>(keys, beg + threadIdx.x, T, end, rn);
 #pragma unroll
-    for (int u = 0; u < U1; u++) {
+    for (int u = 0; u < US; u++) {
         const int64_t i = beg + threadIdx.x + (int64_t)u * T;
         bn[u] = i < end ? bid1[i] : 0u;
     }
-    for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += (int64_t)T * U1) {
-        uint64_t r[U1][W];
-        uint32_t b[U1];
+    for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += (int64_t)T * US) {
+        uint64_t r[US][W];
+        uint32_t b[US];
 #pragma unroll
-        for (int u = 0; u < U1; u++) {
+        for (int u = 0; u < US; u++) {
             b[u] = bn[u];
 #pragma unroll
             for (int w = 0; w < W; w++) r[u][w] = rn[u][w];
         }
-        const int64_t i1 = i0 + (int64_t)T * U1;
-        load_keys<W, U1>(keys, i1, T, end, rn);
+        const int64_t i1 = i0 + (int64_t)T * US;
+        load_keys<W, US>(keys, i1, T, end, rn);
 #pragma unroll
-        for (int u = 0; u < U1; u++) {
+        for (int u = 0; u < US; u++) {
             const int64_t i = i1 + (int64_t)u * T;
             bn[u] = i < end ? bid1[i] : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < U1; u++) {
+        for (int u = 0; u < US; u++) {
             const int64_t i = i0 + (int64_t)u * T;
             if (i < end) {
                 int ones;
@@ -1200,20 +1203,20 @@ __global__ void __launch_bounds__(256)
     unscatter1(const uint32_t *__restrict__ dest1, const uint32_t *__restrict__ U1v, int64_t N,
                IDX *__restrict__ inverse) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < N; i0 += stride * UG) {
-        uint32_t d[UG], u[UG];
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < N; i0 += stride * UG1) {
+        uint32_t d[UG1], u[UG1];
 #pragma unroll
-        for (int q = 0; q < UG; q++) {
+        for (int q = 0; q < UG1; q++) {
             const int64_t i = i0 + q * stride;
             d[q] = i < N ? dest1[i] : 0u;
         }
 #pragma unroll
-        for (int q = 0; q < UG; q++) {
+        for (int q = 0; q < UG1; q++) {
             const int64_t i = i0 + q * stride;
             u[q] = i < N ? U1v[d[q]] : 0u;
         }
 #pragma unroll
-        for (int q = 0; q < UG; q++) {
+        for (int q = 0; q < UG1; q++) {
             const int64_t i = i0 + q * stride;
             if (i < N) inverse[i] = (IDX)u[q];
         }
