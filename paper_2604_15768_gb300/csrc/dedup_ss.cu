@@ -56,7 +56,7 @@ constexpr int WARPS = T / 32;
 constexpr int B2 = 256;
 constexpr int LOG2_B2 = 8;
 using Bid2 = std::conditional<(B2 <= 256), uint8_t, uint16_t>::type;  // leaf id in a bucket
-constexpr int OVS = 4;
+constexpr int OVS = 8;
 constexpr int LEAF_AVG = 1600;
 constexpr int MAX_B1 = 4096;
 constexpr int BT_MAX = 2048;      // binomial-table entries staged in shared memory
@@ -129,7 +129,7 @@ Plan make_plan(int64_t N, int W, int n_bits, int n_ones, int mode, int key_bits)
     p.per_cta = ((N + p.G - 1) / p.G + 31) / 32 * 32;
     // sample sort grid (radix building blocks)
     const int64_t tiles = (p.NS + radix::RTILE - 1) / radix::RTILE;
-    int64_t gs = sm_count();
+    int64_t gs = sm_count() * 4;
     if (gs > tiles) gs = tiles;
     if (gs < 1) gs = 1;
     const int64_t tpc = (tiles + gs - 1) / gs;

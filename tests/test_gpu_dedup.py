@@ -182,7 +182,7 @@ def test_sample_sort_wide_and_overflowing_leaves_vs_oracle():
     wide |= rng.integers(0, 2, size=n).astype(np.uint64)
     wide[::4] = wide[1::4][: wide[::4].size]
     compare(wide.reshape(-1, 1), 64, -1)
-    # sample positions floor(j * N / NS): NS = 4 samples per leaf, 256 leaves
+    # sample positions floor(j * N / NS): NS = 8 samples per leaf, 256 leaves
     # per level-1 bucket, level-1 buckets = the power of two covering
     # ceil(N / 1600) / 256 (the plan of the sample-sort path).  Two heavy keys
     # take turns at those positions, so one leaf spans (2^39, 2^41) with every
@@ -191,7 +191,7 @@ def test_sample_sort_wide_and_overflowing_leaves_vs_oracle():
     b1 = 1
     while b1 < -(-leaves_wanted // 256):
         b1 *= 2
-    ns = min(b1 * 256 * 4, n)
+    ns = min(b1 * 256 * 8, n)
     keys = np.uint64(1 << 40) + rng.permutation(n).astype(np.uint64) * np.uint64(3)
     at = (np.arange(ns, dtype=np.int64) * n) // ns
     keys[at[0::2]] = np.uint64(1 << 39)
