@@ -48,12 +48,12 @@ WORKLOADS = {
              "in HBM (no streaming)",
 }
 
-TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 117.35, "cusci_gen_coupled (fill_kernel)": 15.94}
+TRAFFIC_B_PER_ENTRY = {"cusci_dedup": 117.15, "cusci_gen_coupled (fill_kernel)": 15.93}
 # the same capture per phase of the dedup call (the phase names of
 # cusci_dedup_phase_name; scans and tiny launches folded into their phase)
-DEDUP_KERNEL_B_PER_ENTRY = {"sample+splitters": 0.91, "hist1": 9.95, "scatter1": 25.12,
-                            "level2": 32.76, "leaf_dedup": 14.88, "compact_unique": 5.00,
-                            "unscatter2": 16.81, "unscatter1": 11.91}
+DEDUP_KERNEL_B_PER_ENTRY = {"sample+splitters": 1.93, "hist1": 9.95, "scatter1": 24.21,
+                            "level2": 32.80, "leaf_dedup": 14.54, "compact_unique": 4.99,
+                            "unscatter2": 16.84, "unscatter1": 11.90}
 UNIT = "entries/s"
 
 
